@@ -1,0 +1,174 @@
+/*
+ * hobi.h -- C ABI of the GB300 (sm_103a) HOBI-PB solver library (libhobi.so).
+ *
+ * The library solves the well-posed boundary integral form of the linear
+ * Poisson-Boltzmann equation (W. Geng, "Parallel Higher-order Boundary
+ * Integral Electrostatics Computation on Molecular Surfaces with Curved
+ * Triangulation", Sec. 2.1, Eqs. eqbim_3/eqbim_4) on a closed triangulated
+ * molecular surface, with curved elements built from vertex normals
+ * (Sec. 2.2), 4-point quadrature on regular triangles, 16-point regularised
+ * Gauss-Legendre quadrature on singular triangles (Sec. 2.3), GMRES, and the
+ * electrostatic solvation energy (Sec. 2.5, Eq. solvation_energy).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an int status (hobi_status); nothing throws across the
+ *    ABI. On failure, hobi_last_error() returns a message (thread-local).
+ *  - Units: lengths in Angstrom, charges in e, kappa in 1/Angstrom. The
+ *    unknowns u = [phi; dphi/dnu] (2 N_v doubles: the N_v vertex potentials,
+ *    then the N_v normal derivatives on the inside of the surface) are in the
+ *    units of the formulation (G = 1/(4 pi r)); multiply by HOBI_KCAL_PER_MOL_E
+ *    for kcal/(mol e). Energies are kcal/mol.
+ *  - Dielectric ratio: eps = eps2/eps1 (the paper prints eps1/eps2 after
+ *    Eq_Ls; only eps2/eps1 makes eqbim_3/eqbim_4 consistent with the jump
+ *    condition). Source terms carry 1/eps1.
+ *  - Array arguments (vertices, faces, normals, charges, u, Au, phi, dphi,
+ *    points, potentials) are HOST pointers when opt.mem_device == 0 and
+ *    DEVICE pointers (on the handle's device) when opt.mem_device == 1.
+ *    Scalar outputs (energy, info, counts) are always host pointers.
+ *  - Work is ordered on opt.stream (a cudaStream_t; NULL = the legacy default
+ *    stream). Calls return after their results are complete on that stream
+ *    as far as host pointers are concerned; device-pointer outputs are
+ *    complete in stream order.
+ *  - A handle is not thread-safe: one thread at a time per handle.
+ */
+#ifndef HOBI_H_
+#define HOBI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* 4 pi x 332.0716 kcal A/(mol e^2): formulation units -> kcal/(mol e). */
+#define HOBI_KCAL_PER_MOL_E (4.0 * 3.14159265358979323846 * 332.0716)
+
+typedef struct hobi_ctx* hobi_t;
+
+typedef enum {
+  HOBI_OK = 0,
+  HOBI_ERR_ARG = -1,           /* bad argument (NULL, size, eps <= 0, kappa < 0, NaN) */
+  HOBI_ERR_MESH = -2,          /* mesh not closed, not consistently oriented, bad index, degenerate */
+  HOBI_ERR_CUDA = -3,          /* CUDA runtime error (message names the call) */
+  HOBI_ERR_NOMEM = -4,         /* device allocation failed */
+  HOBI_ERR_NOT_CONVERGED = -5, /* GMRES hit max_it; best iterate written, info filled */
+  HOBI_ERR_BREAKDOWN = -6,     /* GMRES breakdown without convergence */
+  HOBI_ERR_STATE = -7          /* call out of order (e.g. energy before a solve) */
+} hobi_status;
+
+typedef enum {
+  HOBI_FP64 = 0,      /* every pair evaluation in IEEE double */
+  HOBI_FP32_BULK = 1  /* far-field pair sums in FP32 with FP64 tile accumulation; FP64 for
+                         setup, the singular-triangle correction, GMRES and the energy sum */
+} hobi_precision;
+
+typedef struct {
+  int32_t precision;  /* hobi_precision (default HOBI_FP32_BULK) */
+  int32_t mem_device; /* 0: array arguments are host pointers; 1: device pointers */
+  void* stream;       /* cudaStream_t the work is ordered on; NULL: legacy default stream */
+  int32_t restart;    /* GMRES restart length m (default 50, max 200) */
+  int32_t use_graph;  /* 1 (default): replay each GMRES iteration as a captured CUDA graph */
+  int32_t device;     /* CUDA device ordinal; -1 (default): the current device */
+} hobi_options;
+
+typedef struct {
+  int32_t iterations;    /* matvecs spent inside the Krylov iterations */
+  int32_t converged;     /* 1 if ||b - A u|| / ||b|| <= tol (Givens estimate) */
+  double rel_residual;   /* final relative residual estimate */
+  double solve_ms;       /* wall time of hobi_solve on the handle's stream (CUDA events) */
+  double farfield_pairs; /* target-source pair evaluations in the far-field kernel */
+  double* resid_history; /* optional host buffer (caller-owned) for the residual after each it. */
+  int32_t resid_capacity;/* length of resid_history (entries written: min(capacity, iterations+1)) */
+} hobi_solve_info;
+
+/* Fill *opt with the defaults listed in hobi_options. */
+void hobi_default_options(hobi_options* opt);
+
+/* Build a solver for one molecule (Sec. 2.6 routines (1)-(4)).
+ *   vertices       [n_v][3] double, Angstrom.
+ *   faces          [n_f][3] int32, 0-based vertex indices, counter-clockwise seen from outside
+ *                  (the right-hand normal points out of the molecule).
+ *   vertex_normals [n_v][3] double, outward; normalised by the callee.
+ *   charges        [n_c][4] double: x, y, z (Angstrom), q (e). n_c may be 0 (charges NULL).
+ *   eps1, eps2     interior / exterior dielectric constants (> 0); kappa >= 0 (1/A).
+ *   opt            NULL for defaults.
+ * Validates the mesh on the device (indices in range, distinct corners, every directed edge
+ * matched by exactly one opposite edge, no unreferenced vertex, positive enclosed volume,
+ * finite non-zero normals) and returns HOBI_ERR_MESH with a message otherwise.
+ * Copies every input into library-owned device memory; the caller may free its arrays on
+ * return. Then builds the curved elements and quadrature nodes, the vertex-to-face adjacency,
+ * the singular-triangle correction table and the right-hand side [S1; S2] (Eq_Ss).
+ * On success *out owns all device memory until hobi_destroy. */
+int hobi_setup(const double* vertices, int64_t n_v, const int32_t* faces, int64_t n_f,
+               const double* vertex_normals, const double* charges, int64_t n_c, double eps1,
+               double eps2, double kappa, const hobi_options* opt, hobi_t* out);
+
+/* Switch the far-field precision of later matvec/solve/energy calls (hobi_precision). */
+int hobi_set_precision(hobi_t h, int32_t precision);
+
+/* Sizes of the problem (any output pointer may be NULL). n_nodes = 4 n_f quadrature nodes. */
+int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_nodes);
+
+/* One discrete operator application Au = A u (Eqs. eqdbef3-eqdbef6): u and Au are 2 n_v
+ * doubles (layout above). Au must not alias u. */
+int hobi_matvec(hobi_t h, const double* u, double* Au);
+
+/* Right-hand side b = [S1; S2] at the vertices (Eq_Ss), 2 n_v doubles. */
+int hobi_rhs(hobi_t h, double* b);
+
+/* Solve A u = b by GMRES from u = 0 (restart opt.restart) until ||b - A u||/||b|| <= tol or
+ * max_it matvecs. Writes phi (n_v) and dphi (n_v) -- either may be NULL -- and keeps u in the
+ * handle for hobi_energy. Returns HOBI_OK, HOBI_ERR_NOT_CONVERGED (best iterate written) or
+ * HOBI_ERR_BREAKDOWN. info may be NULL. */
+int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi,
+               hobi_solve_info* info);
+
+/* Replace the handle's solution by u (2 n_v doubles), e.g. to evaluate the energy of a given
+ * surface potential. */
+int hobi_set_solution(hobi_t h, const double* u);
+
+/* Copy the handle's solution u (2 n_v doubles) out. */
+int hobi_get_solution(hobi_t h, double* u);
+
+/* Reaction potential phi_reac at n_points points inside the molecule (the integral part of
+ * Eq. solvation_energy, regular rule on every element), from the handle's solution.
+ * points [n_points][3], phi [n_points] (formulation units). */
+int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, double* phi);
+
+/* Electrostatic solvation energy E_sol = (1/2) sum_k q_k phi_reac(x_k) in kcal/mol
+ * (Eq. solvation_energy) from the handle's solution; requires hobi_solve or
+ * hobi_set_solution first (else HOBI_ERR_STATE). e_sol is a host pointer. */
+int hobi_energy(hobi_t h, double* e_sol);
+
+/* Debug/parity accessors (host or device pointers per mem_device, FP64):
+ * quadrature nodes of the regular rule, [n_f][4][3] each: position y_{j,m}, unit normal
+ * nu_{j,m}, and W_{j,m,n} = w_m J_{j,m} L_n(r_m, s_m) (Sec. 2.2, eqdbef3). */
+int hobi_get_nodes(hobi_t h, double* y, double* nu, double* W);
+
+/* Singular-triangle correction table: one entry per (vertex i, face j incident to i), in
+ * vertex order then ascending face index. For entry e: vertex[e] = i, face[e] = j, and
+ * coeff[e][n][k] (k = K1..K4) = (16-point singular rule) - (4-point regular rule) of
+ * sum_m W_{j,m,n} K_k(x_i, y_{j,m}) (Sec. 2.3, eqdbef5/eqdbef6 minus eqdbef3/eqdbef4).
+ * Call with all three arrays NULL to get *n_entries first. Arrays are HOST pointers. */
+int hobi_get_correction(hobi_t h, int64_t* n_entries, int32_t* vertex, int32_t* face,
+                        double* coeff);
+
+/* Far-field kernel timing for roofline measurement: when enabled, CUDA events are recorded
+ * on the launching stream around every far-field launch (GMRES then runs without graph
+ * replay); hobi_profile_read returns the summed kernel milliseconds, the number of launches
+ * and the pair evaluations they did, and resets the counters. */
+int hobi_profile_enable(hobi_t h, int32_t on);
+int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* pairs);
+
+/* Free every resource of the handle (NULL is a no-op). */
+void hobi_destroy(hobi_t h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* hobi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOBI_H_ */

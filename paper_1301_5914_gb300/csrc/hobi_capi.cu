@@ -1,0 +1,709 @@
+// hobi_capi.cu -- the C ABI declared in include/hobi.h: handle lifetime, device memory, stream
+// ordering, the setup pipeline, the matvec pipeline, the GMRES driver (optionally replayed from a
+// captured CUDA graph) and the energy.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "hobi.h"
+#include "hobi_internal.cuh"
+
+using namespace hobi;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define HOBI_CK(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(HOBI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define HOBI_TRY(expr)        \
+  do {                        \
+    int r_ = (expr);          \
+    if (r_ != HOBI_OK) return r_; \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (dev != prev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct hobi_ctx {
+  int device = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  int mem_device = 0, precision = HOBI_FP32_BULK, restart = 50, use_graph = 1;
+  int64_t nv = 0, nf = 0, nc = 0, n_nodes = 0, n_pad = 0;
+  double eps1 = 1, eps2 = 80, kappa = 0, eps = 80;
+  int num_sms = 1;
+  std::vector<void*> allocs;
+  // inputs and geometry
+  double *V = nullptr, *Nin = nullptr, *Nv = nullptr, *Q = nullptr;
+  int *F = nullptr, *deg = nullptr, *inc_ptr = nullptr, *inc_face = nullptr, *entry_vertex = nullptr;
+  double *elem = nullptr, *ny = nullptr, *nnu = nullptr, *nW = nullptr, *corr = nullptr, *b = nullptr;
+  double *center = nullptr, *vol_part = nullptr, *center_part = nullptr;
+  int* flags = nullptr;
+  float4 *tgt32 = nullptr, *ctgt32 = nullptr, *src32 = nullptr, *ptgt32 = nullptr;
+  double *tgt64 = nullptr, *ctgt64 = nullptr, *src64 = nullptr, *ptgt64 = nullptr;
+  double *part = nullptr, *ppart = nullptr, *phi_pts = nullptr, *pts_in = nullptr;
+  size_t ppart_elems = 0, pts_cap = 0;
+  FarFieldPlan plan[2];  // [0] FP64, [1] FP32 -- vertex targets, both rows
+  FarFieldPlan eplan[2]; // charge targets, row 1
+  // iterate vectors
+  double *u_stage = nullptr, *au_stage = nullptr, *x = nullptr, *e_dev = nullptr;
+  bool have_solution = false;
+  // GMRES
+  double *Vb = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *w = nullptr;
+  double *hcol = nullptr, *cvec = nullptr, *dpart = nullptr, *nrm = nullptr;
+  GmresState* st = nullptr;
+  GmresState* st_host = nullptr;  // pinned
+  double* host_scalar = nullptr;  // pinned
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // profiling of the far-field kernel
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  size_t prof_used = 0;
+  double prof_ms = 0.0, prof_pairs = 0.0;
+  int64_t prof_launches = 0;
+  double pending_pairs = 0.0;
+
+  template <class T>
+  int alloc(T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HOBI_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                      cudaGetErrorString(e));
+    }
+    allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return HOBI_OK;
+  }
+
+  void release(void* p) {
+    for (auto& a : allocs)
+      if (a == p) {
+        cudaFree(a);
+        a = nullptr;
+      }
+  }
+
+  // enter: work on the internal stream starts after everything already queued on the user stream
+  int enter() {
+    HOBI_CK(cudaEventRecord(ev_in, user_stream));
+    HOBI_CK(cudaStreamWaitEvent(stream, ev_in, 0));
+    return HOBI_OK;
+  }
+  // leave: the user stream continues after the internal work
+  int leave() {
+    HOBI_CK(cudaEventRecord(ev_out, stream));
+    HOBI_CK(cudaStreamWaitEvent(user_stream, ev_out, 0));
+    return HOBI_OK;
+  }
+
+  int copy_in(double* dst, const double* src, size_t count) {
+    HOBI_CK(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                            mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
+    return HOBI_OK;
+  }
+  int copy_out(double* dst, const double* src, size_t count) {
+    HOBI_CK(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                            mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+    return HOBI_OK;
+  }
+  int finish() {
+    HOBI_TRY(leave());
+    if (!mem_device) HOBI_CK(cudaStreamSynchronize(stream));
+    return HOBI_OK;
+  }
+
+  // --------------------------------------------------------------- matvec pipeline
+  int farfield(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, double* out) {
+    cudaEvent_t a = nullptr, bb = nullptr;
+    if (prof) {
+      if (prof_used == prof_ev.size()) {
+        cudaEvent_t e0, e1;
+        HOBI_CK(cudaEventCreate(&e0));
+        HOBI_CK(cudaEventCreate(&e1));
+        prof_ev.emplace_back(e0, e1);
+      }
+      a = prof_ev[prof_used].first;
+      bb = prof_ev[prof_used].second;
+      ++prof_used;
+      HOBI_CK(cudaEventRecord(a, stream));
+    }
+    HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream));
+    if (prof) {
+      HOBI_CK(cudaEventRecord(bb, stream));
+      pending_pairs += (double)p.n_targets * (double)n_nodes;
+    }
+    return HOBI_OK;
+  }
+
+  // Au = A u with u = base + (*kptr) * ld when kptr is given (device pointers)
+  int matvec_dev(const double* u, const int* kptr, int64_t ld, double* Au) {
+    const bool fp32 = precision == HOBI_FP32_BULK;
+    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, src32,
+                          src64, stream));
+    HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part));
+    HOBI_CK(launch_combine((int)nv, plan[fp32].chunks, part, F, inc_ptr, inc_face, corr, eps, u, kptr, ld, Au,
+                           stream));
+    return HOBI_OK;
+  }
+
+  int collect_profile() {
+    if (!prof || prof_used == 0) return HOBI_OK;
+    HOBI_CK(cudaStreamSynchronize(stream));
+    for (size_t i = 0; i < prof_used; ++i) {
+      float ms = 0.f;
+      HOBI_CK(cudaEventElapsedTime(&ms, prof_ev[i].first, prof_ev[i].second));
+      prof_ms += ms;
+    }
+    prof_launches += (int64_t)prof_used;
+    prof_pairs += pending_pairs;
+    pending_pairs = 0.0;
+    prof_used = 0;
+    return HOBI_OK;
+  }
+
+  // --------------------------------------------------------------- GMRES iteration body
+  int iteration() {
+    const int64_t n = 2 * nv;
+    const int m = restart;
+    HOBI_TRY(matvec_dev(Vb, &st->k, n, w));
+    for (int pass = 0; pass < 2; ++pass) {
+      HOBI_CK(launch_dots(Vb, n, w, n, st, 0, dpart, stream));
+      HOBI_CK(launch_reduce_dots(dpart, m, st, 0, cvec, hcol, pass, stream));
+      HOBI_CK(launch_axpy_basis(Vb, n, cvec, st, w, n, stream));
+    }
+    HOBI_CK(launch_dots(nullptr, 0, w, n, st, 1, dpart, stream));
+    HOBI_CK(launch_reduce_dots(dpart, m, st, 1, nrm, nullptr, 0, stream));
+    HOBI_CK(launch_givens(st, m, H, cs, sn, g, hcol, nrm, stream));
+    HOBI_CK(launch_next_basis(Vb, n, w, n, st, stream));
+    HOBI_CK(launch_advance(st, stream));
+    return HOBI_OK;
+  }
+
+  int run_iteration() {
+    const int pi = precision == HOBI_FP32_BULK;
+    if (!use_graph || prof) return iteration();
+    if (!graph[pi]) {
+      cudaGraph_t gr = nullptr;
+      HOBI_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      int r = iteration();
+      cudaError_t e = cudaStreamEndCapture(stream, &gr);
+      if (r != HOBI_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return r;
+      }
+      if (e != cudaSuccess) return fail(HOBI_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&graph[pi], gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) {
+        graph[pi] = nullptr;
+        return fail(HOBI_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    HOBI_CK(cudaGraphLaunch(graph[pi], stream));
+    return HOBI_OK;
+  }
+
+  int read_state() {
+    HOBI_CK(cudaMemcpyAsync(st_host, st, sizeof(GmresState), cudaMemcpyDeviceToHost, stream));
+    HOBI_CK(cudaStreamSynchronize(stream));
+    return HOBI_OK;
+  }
+
+  int ensure_point_buffers(int64_t np) {
+    if ((size_t)np <= pts_cap) return HOBI_OK;
+    size_t cap = (size_t)np < 64 ? 64 : (size_t)np;
+    if (ptgt32) { release(ptgt32); release(ptgt64); release(phi_pts); release(pts_in); }
+    HOBI_TRY(alloc(&ptgt32, 2 * cap));
+    HOBI_TRY(alloc(&ptgt64, 8 * cap));
+    HOBI_TRY(alloc(&phi_pts, cap));
+    HOBI_TRY(alloc(&pts_in, 3 * cap));
+    pts_cap = cap;
+    return HOBI_OK;
+  }
+  int ensure_ppart(size_t elems) {
+    if (elems <= ppart_elems) return HOBI_OK;
+    if (ppart) release(ppart);
+    HOBI_TRY(alloc(&ppart, elems));
+    ppart_elems = elems;
+    return HOBI_OK;
+  }
+
+  // phi_reac at np targets already in (t32, t64), row 1 only, from the current solution x
+  int reaction_dev(int64_t np, const float4* t32, const double* t64, double* phi) {
+    const bool fp32 = precision == HOBI_FP32_BULK;
+    FarFieldPlan p = plan_farfield(fp32, (int)np, (int)n_pad, false, num_sms, farfield_blocks_per_sm(fp32, false));
+    HOBI_TRY(ensure_ppart((size_t)p.chunks * (size_t)np));
+    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, x, nullptr, 0, src32,
+                          src64, stream));
+    HOBI_TRY(farfield(fp32, p, t32, t64, ppart));
+    HOBI_CK(launch_reduce_points((int)np, p.chunks, ppart, phi, stream));
+    return HOBI_OK;
+  }
+
+  ~hobi_ctx() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& gexec : graph)
+      if (gexec) cudaGraphExecDestroy(gexec);
+    for (void* p : allocs)
+      if (p) cudaFree(p);
+    for (auto& e : prof_ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    if (st_host) cudaFreeHost(st_host);
+    if (host_scalar) cudaFreeHost(host_scalar);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (ev_t0) cudaEventDestroy(ev_t0);
+    if (ev_t1) cudaEventDestroy(ev_t1);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+std::string mesh_message(int fl) {
+  std::string m = "invalid mesh:";
+  if (fl & kBadIndex) m += " face index out of range or repeated within a face;";
+  if (fl & kOpenOrInconsistent) m += " surface not closed or not consistently oriented (a directed edge lacks exactly one opposite edge);";
+  if (fl & kUnreferencedVertex) m += " vertex referenced by no face;";
+  if (fl & kBadNormal) m += " zero or non-finite vertex normal;";
+  if (fl & kNonFinite) m += " non-finite vertex coordinate;";
+  if (fl & kNegativeVolume) m += " enclosed volume not positive (faces must be counter-clockwise seen from outside);";
+  if (fl & kDegenerateFace) m += " zero-area face;";
+  if (fl & kBadCharge) m += " non-finite charge;";
+  return m;
+}
+
+int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const double* normals,
+               const double* charges) {
+  const int64_t nv = h->nv, nf = h->nf, nc = h->nc;
+  const cudaMemcpyKind kind = h->mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  HOBI_TRY(h->alloc(&h->V, 3 * nv));
+  HOBI_TRY(h->alloc(&h->Nin, 3 * nv));
+  HOBI_TRY(h->alloc(&h->Nv, 3 * nv));
+  HOBI_TRY(h->alloc(&h->F, 3 * nf));
+  HOBI_TRY(h->alloc(&h->Q, 4 * (nc > 0 ? nc : 1)));
+  HOBI_TRY(h->alloc(&h->deg, nv));
+  HOBI_TRY(h->alloc(&h->inc_ptr, nv + 1));
+  HOBI_TRY(h->alloc(&h->inc_face, 3 * nf));
+  HOBI_TRY(h->alloc(&h->entry_vertex, 3 * nf));
+  HOBI_TRY(h->alloc(&h->vol_part, 256));
+  HOBI_TRY(h->alloc(&h->center_part, 3 * 256));
+  HOBI_TRY(h->alloc(&h->center, 3));
+  HOBI_TRY(h->alloc(&h->flags, 1));
+  HOBI_CK(cudaMemcpyAsync(h->V, vertices, sizeof(double) * 3 * nv, kind, h->stream));
+  HOBI_CK(cudaMemcpyAsync(h->Nin, normals, sizeof(double) * 3 * nv, kind, h->stream));
+  HOBI_CK(cudaMemcpyAsync(h->F, faces, sizeof(int32_t) * 3 * nf, kind, h->stream));
+  if (nc > 0) HOBI_CK(cudaMemcpyAsync(h->Q, charges, sizeof(double) * 4 * nc, kind, h->stream));
+  HOBI_CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+
+  // adjacency and validation
+  HOBI_CK(launch_adjacency((int)nv, (int)nf, h->F, h->deg, h->inc_ptr, h->inc_face, h->entry_vertex, h->stream));
+  HOBI_CK(launch_validate((int)nv, (int)nf, (int)nc, h->V, h->Nin, h->F, h->inc_ptr, h->inc_face, h->Q, h->Nv,
+                          h->vol_part, 256, h->center_part, h->flags, h->stream));
+  HOBI_CK(launch_finish_validate((int)nv, h->vol_part, 256, h->center_part, h->center, h->flags, h->stream));
+  int flags = 0;
+  HOBI_CK(cudaMemcpyAsync(&flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  HOBI_CK(cudaStreamSynchronize(h->stream));
+  if (flags == kBadCharge) return fail(HOBI_ERR_ARG, "non-finite charge position or value");
+  if (flags) return fail(HOBI_ERR_MESH, mesh_message(flags));
+
+  // curved elements, nodes, correction, right-hand side (Sec. 2.6 routines (1)-(4))
+  h->n_nodes = 4 * nf;
+  h->n_pad = (h->n_nodes + kTile - 1) / kTile * kTile;
+  HOBI_TRY(h->alloc(&h->elem, 30 * nf));
+  HOBI_TRY(h->alloc(&h->ny, 3 * h->n_nodes));
+  HOBI_TRY(h->alloc(&h->nnu, 3 * h->n_nodes));
+  HOBI_TRY(h->alloc(&h->nW, 3 * h->n_nodes));
+  HOBI_TRY(h->alloc(&h->corr, 12 * 3 * nf));
+  HOBI_TRY(h->alloc(&h->b, 2 * nv));
+  HOBI_TRY(h->alloc(&h->tgt32, 2 * nv));
+  HOBI_TRY(h->alloc(&h->tgt64, 8 * nv));
+  HOBI_TRY(h->alloc(&h->ctgt32, 2 * (nc > 0 ? nc : 1)));
+  HOBI_TRY(h->alloc(&h->ctgt64, 8 * (nc > 0 ? nc : 1)));
+  HOBI_TRY(h->alloc(&h->src32, 2 * h->n_pad));
+  HOBI_TRY(h->alloc(&h->src64, 8 * h->n_pad));
+  HOBI_CK(launch_node_gen((int)nf, h->F, h->V, h->Nv, h->center, h->elem, h->ny, h->nnu, h->nW, h->stream));
+  HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem, h->ny,
+                                    h->nnu, h->nW, h->eps, h->kappa, h->corr, h->stream));
+  HOBI_CK(launch_rhs((int)nv, (int)nc, h->V, h->Nv, h->Q, h->eps1, h->b, h->stream));
+  HOBI_CK(launch_targets((int)nv, h->V, h->Nv, h->center, h->tgt32, h->tgt64, h->stream));
+  HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
+  HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
+
+  // far-field plans and partial-sum buffers
+  size_t part_elems = 0;
+  for (int fp32 = 0; fp32 < 2; ++fp32) {
+    h->plan[fp32] = plan_farfield(fp32, (int)nv, (int)h->n_pad, true, h->num_sms, farfield_blocks_per_sm(fp32, true));
+    size_t need = (size_t)h->plan[fp32].chunks * 2 * nv;
+    if (need > part_elems) part_elems = need;
+  }
+  HOBI_TRY(h->alloc(&h->part, part_elems));
+
+  // iterate vectors and GMRES workspace
+  const int64_t n = 2 * nv;
+  const int m = h->restart;
+  HOBI_TRY(h->alloc(&h->u_stage, n));
+  HOBI_TRY(h->alloc(&h->au_stage, n));
+  HOBI_TRY(h->alloc(&h->x, n));
+  HOBI_TRY(h->alloc(&h->e_dev, 1));
+  HOBI_TRY(h->alloc(&h->Vb, (size_t)(m + 1) * n));
+  HOBI_TRY(h->alloc(&h->H, (size_t)(m + 1) * m));
+  HOBI_TRY(h->alloc(&h->cs, m));
+  HOBI_TRY(h->alloc(&h->sn, m));
+  HOBI_TRY(h->alloc(&h->g, m + 1));
+  HOBI_TRY(h->alloc(&h->y, m));
+  HOBI_TRY(h->alloc(&h->w, n));
+  HOBI_TRY(h->alloc(&h->hcol, m + 1));
+  HOBI_TRY(h->alloc(&h->cvec, m + 1));
+  HOBI_TRY(h->alloc(&h->nrm, 1));
+  HOBI_TRY(h->alloc(&h->dpart, (size_t)(m + 1) * kDotBlocks));
+  HOBI_TRY(h->alloc(&h->st, 1));
+  HOBI_CK(cudaMallocHost(&h->st_host, sizeof(GmresState)));
+  HOBI_CK(cudaMallocHost(&h->host_scalar, sizeof(double)));
+  HOBI_CK(cudaMemsetAsync(h->H, 0, sizeof(double) * (m + 1) * m, h->stream));
+  HOBI_CK(cudaStreamSynchronize(h->stream));
+  return HOBI_OK;
+}
+
+bool bad_ptr_arg(const void* p) { return p == nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+void hobi_default_options(hobi_options* opt) {
+  if (!opt) return;
+  opt->precision = HOBI_FP32_BULK;
+  opt->mem_device = 0;
+  opt->stream = nullptr;
+  opt->restart = 50;
+  opt->use_graph = 1;
+  opt->device = -1;
+}
+
+const char* hobi_last_error(void) { return g_err.c_str(); }
+
+int hobi_setup(const double* vertices, int64_t n_v, const int32_t* faces, int64_t n_f, const double* vertex_normals,
+               const double* charges, int64_t n_c, double eps1, double eps2, double kappa, const hobi_options* opt,
+               hobi_t* out) {
+  g_err.clear();
+  if (!out) return fail(HOBI_ERR_ARG, "out handle pointer is NULL");
+  *out = nullptr;
+  if (bad_ptr_arg(vertices) || bad_ptr_arg(faces) || bad_ptr_arg(vertex_normals))
+    return fail(HOBI_ERR_ARG, "vertices, faces and vertex_normals must be non-NULL");
+  if (n_c > 0 && !charges) return fail(HOBI_ERR_ARG, "charges is NULL but n_c > 0");
+  if (n_v < 4 || n_f < 4) return fail(HOBI_ERR_ARG, "a closed surface needs at least 4 vertices and 4 faces");
+  if (n_c < 0) return fail(HOBI_ERR_ARG, "n_c < 0");
+  if (n_f > (int64_t(1) << 28) || n_v > (int64_t(1) << 28) || n_c > (int64_t(1) << 28))
+    return fail(HOBI_ERR_ARG, "problem too large (n_v, n_f, n_c must be < 2^28)");
+  if (!(eps1 > 0.0) || !(eps2 > 0.0) || !isfinite(eps1) || !isfinite(eps2))
+    return fail(HOBI_ERR_ARG, "eps1 and eps2 must be finite and > 0");
+  if (!(kappa >= 0.0) || !isfinite(kappa)) return fail(HOBI_ERR_ARG, "kappa must be finite and >= 0");
+  hobi_options o;
+  hobi_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != HOBI_FP64 && o.precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
+  if (o.restart <= 0) o.restart = 50;
+  if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
+
+  int dev = o.device;
+  if (dev < 0) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(HOBI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  DeviceGuard guard(dev);
+  hobi_ctx* h = new hobi_ctx();
+  h->device = dev;
+  h->user_stream = static_cast<cudaStream_t>(o.stream);
+  h->mem_device = o.mem_device ? 1 : 0;
+  h->precision = o.precision;
+  h->restart = o.restart;
+  h->use_graph = o.use_graph ? 1 : 0;
+  h->nv = n_v;
+  h->nf = n_f;
+  h->nc = n_c;
+  h->eps1 = eps1;
+  h->eps2 = eps2;
+  h->kappa = kappa;
+  h->eps = eps2 / eps1;
+  int r = HOBI_OK;
+  do {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+      r = fail(HOBI_ERR_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(e));
+      break;
+    }
+    r = h->enter();
+    if (r != HOBI_OK) break;
+    r = setup_impl(h, vertices, faces, vertex_normals, charges);
+    if (r != HOBI_OK) break;
+    r = h->leave();
+  } while (0);
+  if (r != HOBI_OK) {
+    std::string msg = g_err;
+    delete h;
+    g_err = msg;
+    return r;
+  }
+  *out = h;
+  return HOBI_OK;
+}
+
+int hobi_set_precision(hobi_t h, int32_t precision) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (precision != HOBI_FP64 && precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
+  h->precision = precision;
+  return HOBI_OK;
+}
+
+int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_nodes) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (n_v) *n_v = h->nv;
+  if (n_f) *n_f = h->nf;
+  if (n_c) *n_c = h->nc;
+  if (n_nodes) *n_nodes = h->n_nodes;
+  return HOBI_OK;
+}
+
+int hobi_matvec(hobi_t h, const double* u, double* Au) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (!u || !Au) return fail(HOBI_ERR_ARG, "u and Au must be non-NULL");
+  if (u == Au) return fail(HOBI_ERR_ARG, "Au must not alias u");
+  DeviceGuard guard(h->device);
+  const int64_t n = 2 * h->nv;
+  HOBI_TRY(h->enter());
+  const double* ud = u;
+  double* ad = Au;
+  if (!h->mem_device) {
+    HOBI_CK(cudaMemcpyAsync(h->u_stage, u, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    ud = h->u_stage;
+    ad = h->au_stage;
+  }
+  HOBI_TRY(h->matvec_dev(ud, nullptr, 0, ad));
+  if (!h->mem_device) HOBI_CK(cudaMemcpyAsync(Au, ad, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  HOBI_TRY(h->finish());
+  HOBI_TRY(h->collect_profile());
+  return HOBI_OK;
+}
+
+int hobi_rhs(hobi_t h, double* b) {
+  if (!h || !b) return fail(HOBI_ERR_ARG, "NULL argument");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->copy_out(b, h->b, 2 * h->nv));
+  return h->finish();
+}
+
+int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, hobi_solve_info* info) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (!(tol > 0.0) || max_it < 1) return fail(HOBI_ERR_ARG, "need tol > 0 and max_it >= 1");
+  DeviceGuard guard(h->device);
+  const int64_t n = 2 * h->nv;
+  const int m = h->restart;
+  HOBI_TRY(h->enter());
+  HOBI_CK(cudaEventRecord(h->ev_t0, h->stream));
+  // initial state: x = 0, r = b
+  GmresState s0;
+  memset(&s0, 0, sizeof s0);
+  s0.tol = tol;
+  *h->st_host = s0;
+  HOBI_CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(GmresState), cudaMemcpyHostToDevice, h->stream));
+  HOBI_CK(cudaMemsetAsync(h->x, 0, sizeof(double) * n, h->stream));
+  HOBI_CK(cudaMemcpyAsync(h->Vb, h->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  HOBI_CK(launch_dots(nullptr, 0, h->Vb, n, h->st, 1, h->dpart, h->stream));
+  HOBI_CK(launch_reduce_dots(h->dpart, m, h->st, 1, h->nrm, nullptr, 0, h->stream));
+  HOBI_CK(launch_cycle_start(h->Vb, n, h->nrm, h->st, h->g, m, 1, h->stream));
+  HOBI_TRY(h->read_state());
+  std::vector<double> hist;
+  hist.push_back(h->st_host->rel);
+  bool done = h->st_host->converged || h->st_host->breakdown;
+  while (!done) {
+    for (int kk = 0; kk < m; ++kk) {
+      if (h->st_host->it >= max_it) break;
+      HOBI_TRY(h->run_iteration());
+      HOBI_TRY(h->read_state());
+      hist.push_back(h->st_host->rel);
+      if (h->st_host->converged || h->st_host->breakdown) break;
+    }
+    HOBI_CK(launch_finish_cycle(h->H, m, h->g, h->st, h->y, h->Vb, n, h->x, n, h->stream));
+    if (h->st_host->converged || h->st_host->breakdown || h->st_host->it >= max_it) break;
+    // restart from r = b - A x
+    HOBI_TRY(h->matvec_dev(h->x, nullptr, 0, h->w));
+    HOBI_CK(launch_residual_start(h->b, h->w, h->Vb, n, h->stream));
+    HOBI_CK(launch_dots(nullptr, 0, h->Vb, n, h->st, 1, h->dpart, h->stream));
+    HOBI_CK(launch_reduce_dots(h->dpart, m, h->st, 1, h->nrm, nullptr, 0, h->stream));
+    HOBI_CK(launch_cycle_start(h->Vb, n, h->nrm, h->st, h->g, m, 0, h->stream));
+    HOBI_TRY(h->read_state());
+    done = h->st_host->converged || h->st_host->breakdown;
+  }
+  HOBI_CK(cudaEventRecord(h->ev_t1, h->stream));
+  if (phi) HOBI_TRY(h->copy_out(phi, h->x, h->nv));
+  if (dphi) HOBI_TRY(h->copy_out(dphi, h->x + h->nv, h->nv));
+  HOBI_TRY(h->finish());
+  HOBI_CK(cudaEventSynchronize(h->ev_t1));
+  HOBI_TRY(h->collect_profile());
+  h->have_solution = true;
+  const GmresState fs = *h->st_host;
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
+    info->iterations = fs.it;
+    info->converged = fs.converged;
+    info->rel_residual = fs.rel;
+    info->solve_ms = ms;
+    info->farfield_pairs = (double)(fs.it + 0) * (double)h->nv * (double)h->n_nodes;
+    if (info->resid_history && info->resid_capacity > 0) {
+      int cnt = (int)hist.size() < info->resid_capacity ? (int)hist.size() : info->resid_capacity;
+      for (int i = 0; i < cnt; ++i) info->resid_history[i] = hist[i];
+    }
+  }
+  if (fs.converged) return HOBI_OK;
+  if (fs.breakdown) return fail(HOBI_ERR_BREAKDOWN, "GMRES breakdown (zero or non-finite Arnoldi norm)");
+  return fail(HOBI_ERR_NOT_CONVERGED, "GMRES did not reach tol within max_it iterations (rel residual " +
+                                          std::to_string(fs.rel) + ")");
+}
+
+int hobi_set_solution(hobi_t h, const double* u) {
+  if (!h || !u) return fail(HOBI_ERR_ARG, "NULL argument");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->copy_in(h->x, u, 2 * h->nv));
+  HOBI_TRY(h->finish());
+  h->have_solution = true;
+  return HOBI_OK;
+}
+
+int hobi_get_solution(hobi_t h, double* u) {
+  if (!h || !u) return fail(HOBI_ERR_ARG, "NULL argument");
+  if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->copy_out(u, h->x, 2 * h->nv));
+  return h->finish();
+}
+
+int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, double* phi) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (n_points < 0 || (n_points > 0 && (!points || !phi))) return fail(HOBI_ERR_ARG, "bad points/phi arguments");
+  if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
+  if (n_points == 0) return HOBI_OK;
+  if (n_points > (int64_t(1) << 28)) return fail(HOBI_ERR_ARG, "too many points");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->ensure_point_buffers(n_points));
+  HOBI_TRY(h->copy_in(h->pts_in, points, 3 * n_points));
+  HOBI_CK(launch_points((int)n_points, h->pts_in, 3, h->center, h->ptgt32, h->ptgt64, h->stream));
+  HOBI_TRY(h->reaction_dev(n_points, h->ptgt32, h->ptgt64, h->phi_pts));
+  HOBI_TRY(h->copy_out(phi, h->phi_pts, n_points));
+  HOBI_TRY(h->finish());
+  HOBI_TRY(h->collect_profile());
+  return HOBI_OK;
+}
+
+int hobi_energy(hobi_t h, double* e_sol) {
+  if (!h || !e_sol) return fail(HOBI_ERR_ARG, "NULL argument");
+  if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
+  DeviceGuard guard(h->device);
+  if (h->nc == 0) {
+    *e_sol = 0.0;
+    return HOBI_OK;
+  }
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->ensure_point_buffers(h->nc));
+  HOBI_TRY(h->reaction_dev(h->nc, h->ctgt32, h->ctgt64, h->phi_pts));
+  HOBI_CK(launch_energy_sum((int)h->nc, h->Q, h->phi_pts, h->e_dev, h->stream));
+  HOBI_CK(cudaMemcpyAsync(h->host_scalar, h->e_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  HOBI_TRY(h->leave());
+  HOBI_CK(cudaStreamSynchronize(h->stream));
+  HOBI_TRY(h->collect_profile());
+  *e_sol = *h->host_scalar;
+  return HOBI_OK;
+}
+
+int hobi_get_nodes(hobi_t h, double* y, double* nu, double* W) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  if (y) HOBI_TRY(h->copy_out(y, h->ny, 3 * h->n_nodes));
+  if (nu) HOBI_TRY(h->copy_out(nu, h->nnu, 3 * h->n_nodes));
+  if (W) HOBI_TRY(h->copy_out(W, h->nW, 3 * h->n_nodes));
+  return h->finish();
+}
+
+int hobi_get_correction(hobi_t h, int64_t* n_entries, int32_t* vertex, int32_t* face, double* coeff) {
+  if (!h || !n_entries) return fail(HOBI_ERR_ARG, "NULL argument");
+  *n_entries = 3 * h->nf;
+  if (!vertex && !face && !coeff) return HOBI_OK;
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  const size_t ne = (size_t)(3 * h->nf);
+  if (vertex) HOBI_CK(cudaMemcpyAsync(vertex, h->entry_vertex, sizeof(int) * ne, cudaMemcpyDeviceToHost, h->stream));
+  if (face) HOBI_CK(cudaMemcpyAsync(face, h->inc_face, sizeof(int) * ne, cudaMemcpyDeviceToHost, h->stream));
+  if (coeff) HOBI_CK(cudaMemcpyAsync(coeff, h->corr, sizeof(double) * 12 * ne, cudaMemcpyDeviceToHost, h->stream));
+  HOBI_TRY(h->leave());
+  HOBI_CK(cudaStreamSynchronize(h->stream));
+  return HOBI_OK;
+}
+
+int hobi_profile_enable(hobi_t h, int32_t on) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  h->prof = on != 0;
+  return HOBI_OK;
+}
+
+int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* pairs) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->collect_profile());
+  if (farfield_ms) *farfield_ms = h->prof_ms;
+  if (launches) *launches = h->prof_launches;
+  if (pairs) *pairs = h->prof_pairs;
+  h->prof_ms = 0.0;
+  h->prof_launches = 0;
+  h->prof_pairs = 0.0;
+  return HOBI_OK;
+}
+
+void hobi_destroy(hobi_t h) {
+  if (!h) return;
+  DeviceGuard guard(h->device);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// hobi_internal.cuh -- declarations shared by the CUDA translation units of libhobi.
+//
+// Data layout in device memory (per handle):
+//   V[n_v][3], Nv[n_v][3] (unit), F[n_f][3], Q[n_c][4]        FP64 / int32 inputs
+//   elem[n_f][10][3]          the 10 interpolation points of each curved element (FP64)
+//   ny[n_n][3], nnu[n_n][3], nW[n_n][3]                        regular-rule nodes, n_n = 4 n_f,
+//                                                              node index = 4 j + m (FP64)
+//   inc_ptr[n_v+1], inc_face[3 n_f]                            vertex -> incident faces (sorted)
+//   corr[3 n_f][3][4]         singular correction per (vertex, incident face) entry (FP64)
+//   tgt32[n_v][2] float4      target x - c and unit normal (FP32 path)
+//   src32[n_pad][2] float4    (y - c, sigma/4pi), (mu nu_y/4pi, 0) per node, rebuilt per matvec
+//   src64[n_pad][8] double    (y - c, sigma/4pi, mu nu_y/4pi, 0) per node (FP64 path)
+//   part[chunks][2 n_v]       FP64 far-field partial sums per source chunk
+// c is the vertex centroid: both precisions work in coordinates relative to it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hobi {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 1.0 / (4.0 * 3.14159265358979323846);
+constexpr double kCoulomb = 332.0716;  // kcal A / (mol e^2)
+
+// Far-field tiling (FP32): threads per block, targets per thread, source nodes per smem tile.
+constexpr int kFF32Threads = 256;
+constexpr int kFF32Targets = 4;
+constexpr int kTile = 256;
+// FP64 path
+constexpr int kFF64Threads = 128;
+constexpr int kFF64Targets = 2;
+
+// Mesh validation flag bits (setup).
+enum MeshFlag : int {
+  kBadIndex = 1,
+  kOpenOrInconsistent = 2,
+  kUnreferencedVertex = 4,
+  kBadNormal = 8,
+  kNonFinite = 16,
+  kNegativeVolume = 32,
+  kDegenerateFace = 64,
+  kBadCharge = 128,
+};
+
+// ---- setup kernels (k_setup.cu) ----
+// builds inc_ptr/inc_face (rows sorted by face) and entry_vertex[3 nf] (entry -> vertex)
+cudaError_t launch_adjacency(int nv, int nf, const int* F, int* deg, int* inc_ptr, int* inc_face,
+                             int* entry_vertex, cudaStream_t s);
+cudaError_t launch_validate(int nv, int nf, int nc, const double* V, const double* Nv_in, const int* F,
+                            const int* inc_ptr, const int* inc_face, const double* Q, double* Nv_unit,
+                            double* vol_part, int vol_blocks, double* center_part, int* flags,
+                            cudaStream_t s);
+cudaError_t launch_finish_validate(int nv, const double* vol_part, int vol_blocks, const double* center_part,
+                                   double* center, int* flags, cudaStream_t s);
+cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double* Nv, const double* center,
+                            double* elem, double* ny, double* nnu, double* nW, cudaStream_t s);
+// one thread per (vertex, incident face) entry; vert[e] is the entry's vertex
+cudaError_t launch_correction_entries(int n_entries, const int* vert, const int* F, const double* V,
+                                      const double* Nv, const int* inc_face, const double* elem, const double* ny,
+                                      const double* nnu, const double* nW, double eps, double kappa, double* corr,
+                                      cudaStream_t s);
+cudaError_t launch_rhs(int nv, int nc, const double* V, const double* Nv, const double* Q, double eps1,
+                       double* b, cudaStream_t s);
+cudaError_t launch_targets(int nv, const double* V, const double* Nv, const double* center, float4* tgt32,
+                           double* tgt64, cudaStream_t s);
+cudaError_t launch_points(int np, const double* P, int stride, const double* center, float4* tgt32,
+                          double* tgt64, cudaStream_t s);
+
+// ---- far field (k_farfield.cu) ----
+// Source densities of the current iterate u (2 n_v) for every node; padded nodes stay inert.
+// If kptr != nullptr the vector is u + (*kptr) * ld (GMRES basis column).
+cudaError_t launch_gather(bool fp32, int n_nodes, int n_pad, int nv, const int* F, const double* ny,
+                          const double* nnu, const double* nW, const double* center, const double* u,
+                          const int* kptr, int64_t ld, float4* src32, double* src64, cudaStream_t s);
+cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* src64, cudaStream_t s);
+
+struct FarFieldPlan {
+  int n_targets;
+  int n_tiles;          // source tiles of kTile nodes
+  int tiles_per_chunk;
+  int chunks;
+  bool row2;            // compute the second row (K3, K4) too
+};
+FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2, int num_sms,
+                           int blocks_per_sm);
+int farfield_blocks_per_sm(bool fp32, bool row2);
+cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt32, const double* tgt64,
+                            const float4* src32, const double* src64, double eps, double kappa,
+                            double* part, cudaStream_t s);
+// Au = diag u - (sum of chunk partials + singular correction)  (rows i and n_v + i)
+cudaError_t launch_combine(int nv, int chunks, const double* part, const int* F, const int* inc_ptr,
+                           const int* inc_face, const double* corr, double eps, const double* u,
+                           const int* kptr, int64_t ld, double* Au, cudaStream_t s);
+// phi[k] = sum over chunks of part[c][k]; then e = 0.5 * 4 pi C * sum_k q_k phi[k]
+cudaError_t launch_reduce_points(int np, int chunks, const double* part, double* phi, cudaStream_t s);
+cudaError_t launch_energy_sum(int nc, const double* Q, const double* phi, double* e, cudaStream_t s);
+
+// ---- GMRES (k_gmres.cu) ----
+struct GmresState {
+  int k;          // column being built in the current cycle
+  int it;         // total Krylov iterations
+  int converged;
+  int breakdown;
+  double bnorm;
+  double rel;     // |g_{k+1}| / ||b||
+  double tol;
+  double hn;      // last h_{k+1,k}
+};
+constexpr int kDotBlocks = 296;
+cudaError_t launch_dots(const double* Vb, int64_t ld, const double* w, int64_t n, const GmresState* st,
+                        int self, double* part, cudaStream_t s);
+cudaError_t launch_reduce_dots(const double* part, int m, const GmresState* st, int self, double* c,
+                               double* hcol, int accumulate, cudaStream_t s);
+cudaError_t launch_axpy_basis(const double* Vb, int64_t ld, const double* c, const GmresState* st, double* w,
+                              int64_t n, cudaStream_t s);
+cudaError_t launch_givens(GmresState* st, int m, double* H, double* cs, double* sn, double* g,
+                          const double* hcol, const double* hn2, cudaStream_t s);
+cudaError_t launch_next_basis(double* Vb, int64_t ld, const double* w, int64_t n, GmresState* st,
+                              cudaStream_t s);
+cudaError_t launch_advance(GmresState* st, cudaStream_t s);
+cudaError_t launch_cycle_start(double* Vb, int64_t n, const double* nrm2, GmresState* st, double* g, int m,
+                               int first, cudaStream_t s);
+cudaError_t launch_finish_cycle(const double* H, int m, const double* g, const GmresState* st, double* y,
+                                const double* Vb, int64_t ld, double* x, int64_t n, cudaStream_t s);
+cudaError_t launch_residual_start(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t s);
+
+}  // namespace hobi

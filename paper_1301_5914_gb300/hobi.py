@@ -1,0 +1,272 @@
+"""Thin Python binding of libhobi (include/hobi.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA library. Inputs may be numpy arrays
+(host pointers: the library copies them to and from the GPU) or CUDA torch
+tensors (device pointers, work ordered on torch's current stream). PyTorch is
+used only for device memory and streams.
+
+If ``_build/libhobi.so`` is missing this module raises on first use: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libhobi.so")
+
+HOBI_OK = 0
+HOBI_ERR_ARG = -1
+HOBI_ERR_MESH = -2
+HOBI_ERR_CUDA = -3
+HOBI_ERR_NOMEM = -4
+HOBI_ERR_NOT_CONVERGED = -5
+HOBI_ERR_BREAKDOWN = -6
+HOBI_ERR_STATE = -7
+HOBI_FP64 = 0
+HOBI_FP32_BULK = 1
+KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
+
+EXPORTS = [
+    "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
+    "hobi_solve", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential", "hobi_energy",
+    "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_destroy",
+    "hobi_last_error",
+]
+
+
+class HobiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hobi error {code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("mem_device", C.c_int32), ("stream", C.c_void_p),
+                ("restart", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
+                ("solve_ms", C.c_double), ("farfield_pairs", C.c_double),
+                ("resid_history", C.POINTER(C.c_double)), ("resid_capacity", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhobi.so and declare its signatures (fails loudly if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhobi.so not found at {path}; build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = C.CDLL(path)
+    vp, dp, i64 = C.c_void_p, C.c_void_p, C.c_int64
+    lib.hobi_default_options.argtypes = [C.POINTER(Options)]
+    lib.hobi_default_options.restype = None
+    lib.hobi_setup.argtypes = [dp, i64, dp, i64, dp, dp, i64, C.c_double, C.c_double, C.c_double,
+                               C.POINTER(Options), C.POINTER(C.c_void_p)]
+    lib.hobi_set_precision.argtypes = [vp, C.c_int32]
+    lib.hobi_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    lib.hobi_matvec.argtypes = [vp, dp, dp]
+    lib.hobi_rhs.argtypes = [vp, dp]
+    lib.hobi_solve.argtypes = [vp, C.c_double, C.c_int32, dp, dp, C.POINTER(SolveInfo)]
+    lib.hobi_set_solution.argtypes = [vp, dp]
+    lib.hobi_get_solution.argtypes = [vp, dp]
+    lib.hobi_reaction_potential.argtypes = [vp, dp, i64, dp]
+    lib.hobi_energy.argtypes = [vp, C.POINTER(C.c_double)]
+    lib.hobi_get_nodes.argtypes = [vp, dp, dp, dp]
+    lib.hobi_get_correction.argtypes = [vp, C.POINTER(i64), dp, dp, dp]
+    lib.hobi_profile_enable.argtypes = [vp, C.c_int32]
+    lib.hobi_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(C.c_double)]
+    lib.hobi_destroy.argtypes = [vp]
+    lib.hobi_destroy.restype = None
+    lib.hobi_last_error.argtypes = []
+    lib.hobi_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("hobi_default_options", "hobi_destroy", "hobi_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != HOBI_OK:
+        raise HobiError(code, _lib.hobi_last_error().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One molecule on one GPU (wraps a hobi_t handle).
+
+    V [n_v,3], F [n_f,3] int32, N [n_v,3], charges [n_c,4]: all numpy arrays
+    (host mode) or all CUDA torch tensors (device mode).
+    """
+
+    def __init__(self, V, F, N, charges, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
+                 restart: int = 50, use_graph: bool = True, device: int | None = None, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.device_mode = _is_torch(V)
+        opt = Options()
+        lib.hobi_default_options(C.byref(opt))
+        opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
+        opt.restart = int(restart)
+        opt.use_graph = 1 if use_graph else 0
+        if self.device_mode:
+            import torch
+
+            dev = V.device.index if device is None else device
+            opt.device = int(dev if dev is not None else torch.cuda.current_device())
+            opt.mem_device = 1
+            s = stream if stream is not None else torch.cuda.current_stream(opt.device)
+            opt.stream = C.c_void_p(s.cuda_stream)
+            self._keep = [t.contiguous() for t in (V, F, N, charges)]
+            Vt, Ft, Nt, Qt = self._keep
+            assert Vt.dtype == torch.float64 and Nt.dtype == torch.float64 and Qt.dtype == torch.float64
+            assert Ft.dtype == torch.int32
+            ptrs = [Vt.data_ptr(), Ft.data_ptr(), Nt.data_ptr(), Qt.data_ptr() if Qt.numel() else None]
+            nv, nf, nc = Vt.shape[0], Ft.shape[0], Qt.reshape(-1, 4).shape[0]
+        else:
+            opt.device = -1 if device is None else int(device)
+            opt.mem_device = 0
+            self._keep = [np.ascontiguousarray(V, dtype=np.float64), np.ascontiguousarray(F, dtype=np.int32),
+                          np.ascontiguousarray(N, dtype=np.float64),
+                          np.ascontiguousarray(charges, dtype=np.float64).reshape(-1, 4)]
+            Va, Fa, Na, Qa = self._keep
+            ptrs = [Va.ctypes.data, Fa.ctypes.data, Na.ctypes.data, Qa.ctypes.data if Qa.size else None]
+            nv, nf, nc = Va.shape[0], Fa.shape[0], Qa.shape[0]
+        h = C.c_void_p()
+        _check(lib.hobi_setup(ptrs[0], nv, ptrs[1], nf, ptrs[2], ptrs[3], nc, float(eps1), float(eps2),
+                              float(kappa), C.byref(opt), C.byref(h)))
+        self._h = h
+        self.nv, self.nf, self.nc = int(nv), int(nf), int(nc)
+        self.n_nodes = 4 * self.nf
+        self.eps1, self.eps2, self.kappa = float(eps1), float(eps2), float(kappa)
+
+    # ------------------------------------------------------------ helpers
+    def _out(self, n, like=None):
+        if self.device_mode:
+            import torch
+
+            return torch.empty(n, dtype=torch.float64, device=self._keep[0].device)
+        return np.empty(n, dtype=np.float64)
+
+    def _ptr(self, a):
+        if self.device_mode:
+            return a.data_ptr()
+        return a.ctypes.data
+
+    def _in(self, a, n):
+        if self.device_mode:
+            import torch
+
+            t = a if _is_torch(a) else torch.as_tensor(np.asarray(a))
+            t = t.to(device=self._keep[0].device, dtype=torch.float64).contiguous().reshape(-1)
+            assert t.numel() == n
+            return t
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        assert a.size == n
+        return a
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hobi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ API
+    def set_precision(self, precision: str):
+        _check(self._lib.hobi_set_precision(self._h, HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64))
+
+    def matvec(self, u):
+        u = self._in(u, 2 * self.nv)
+        out = self._out(2 * self.nv)
+        _check(self._lib.hobi_matvec(self._h, self._ptr(u), self._ptr(out)))
+        return out
+
+    def rhs(self):
+        out = self._out(2 * self.nv)
+        _check(self._lib.hobi_rhs(self._h, self._ptr(out)))
+        return out
+
+    def solve(self, tol: float = 1e-6, max_it: int = 200, history: int = 0, raise_on_fail: bool = True):
+        """Returns (phi, dphi, info dict). info['status'] holds the return code."""
+        phi = self._out(self.nv)
+        dphi = self._out(self.nv)
+        info = SolveInfo()
+        hist = None
+        if history > 0:
+            hist = (C.c_double * history)()
+            info.resid_history = C.cast(hist, C.POINTER(C.c_double))
+            info.resid_capacity = history
+        code = self._lib.hobi_solve(self._h, float(tol), int(max_it), self._ptr(phi), self._ptr(dphi),
+                                    C.byref(info))
+        if raise_on_fail and code not in (HOBI_OK,):
+            _check(code)
+        d = {"status": code, "iterations": info.iterations, "converged": bool(info.converged),
+             "rel_residual": info.rel_residual, "solve_ms": info.solve_ms, "farfield_pairs": info.farfield_pairs}
+        if hist is not None:
+            d["history"] = np.array(hist[: min(history, info.iterations + 1)])
+        return phi, dphi, d
+
+    def set_solution(self, u):
+        u = self._in(u, 2 * self.nv)
+        _check(self._lib.hobi_set_solution(self._h, self._ptr(u)))
+
+    def solution(self):
+        out = self._out(2 * self.nv)
+        _check(self._lib.hobi_get_solution(self._h, self._ptr(out)))
+        return out
+
+    def reaction_potential(self, points):
+        n = int(np.prod(points.shape)) // 3
+        p = self._in(points, 3 * n)
+        out = self._out(n)
+        _check(self._lib.hobi_reaction_potential(self._h, self._ptr(p), n, self._ptr(out)))
+        return out
+
+    def energy(self) -> float:
+        e = C.c_double()
+        _check(self._lib.hobi_energy(self._h, C.byref(e)))
+        return float(e.value)
+
+    def nodes(self):
+        """(y, nu, W), each [n_f, 4, 3] FP64."""
+        outs = [self._out(3 * self.n_nodes) for _ in range(3)]
+        _check(self._lib.hobi_get_nodes(self._h, *[self._ptr(o) for o in outs]))
+        return tuple(o.reshape(self.nf, 4, 3) for o in outs)
+
+    def correction(self):
+        """(vertex[e], face[e], coeff[e,3,4]) for every (vertex, incident face) entry."""
+        n = C.c_int64()
+        _check(self._lib.hobi_get_correction(self._h, C.byref(n), None, None, None))
+        ne = n.value
+        v = np.empty(ne, dtype=np.int32)
+        f = np.empty(ne, dtype=np.int32)
+        c = np.empty((ne, 3, 4), dtype=np.float64)
+        _check(self._lib.hobi_get_correction(self._h, C.byref(n), v.ctypes.data, f.ctypes.data, c.ctypes.data))
+        return v, f, c
+
+    def profile_enable(self, on: bool = True):
+        _check(self._lib.hobi_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        ms, pairs = C.c_double(), C.c_double()
+        n = C.c_int64()
+        _check(self._lib.hobi_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(pairs)))
+        return {"farfield_ms": ms.value, "launches": n.value, "pairs": pairs.value}
