@@ -155,11 +155,16 @@ int hobi_get_correction(hobi_t h, int64_t* n_entries, int32_t* vertex, int32_t* 
                         double* coeff);
 
 /* Far-field kernel timing for roofline measurement: when enabled, CUDA events are recorded
- * on the launching stream around every far-field launch (GMRES then runs without graph
- * replay); hobi_profile_read returns the summed kernel milliseconds, the number of launches
- * and the pair evaluations they did, and resets the counters. */
+ * on the launching stream around every far-field launch (inside the captured GMRES graph as
+ * event-record nodes when graphs are in use); hobi_profile_read returns the summed kernel
+ * milliseconds, the number of launches and the pair evaluations they did, and resets the
+ * counters. */
 int hobi_profile_enable(hobi_t h, int32_t on);
 int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* pairs);
+
+/* Number of CUDA kernels this handle has launched since hobi_setup began (setup included;
+ * a replayed GMRES graph counts each of its kernels). */
+int hobi_kernel_launches(hobi_t h, int64_t* n);
 
 /* Free every resource of the handle (NULL is a no-op). */
 void hobi_destroy(hobi_t h);

@@ -79,7 +79,14 @@ struct hobi_ctx {
   GmresState* st = nullptr;
   GmresState* st_host = nullptr;  // pinned
   double* host_scalar = nullptr;  // pinned
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // captured GMRES iteration per [precision][profiling]; the profiling variant carries event
+  // record nodes around the far-field launch (gev), read after every replay
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaEvent_t gev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  double graph_pairs[2] = {0.0, 0.0};
+  bool replay_prof_pending = false;
+  bool graph_timing_unavailable = false;  // set if events inside graphs cannot be timed
+  int replay_prof_pi = 0;
   // profiling of the far-field kernel
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
@@ -87,6 +94,11 @@ struct hobi_ctx {
   double prof_ms = 0.0, prof_pairs = 0.0;
   int64_t prof_launches = 0;
   double pending_pairs = 0.0;
+  int64_t launches = 0;  // kernels this handle launched (graph replays count their kernels)
+  bool capturing = false;
+  // kernels in one GMRES iteration: gather, far field, combine, 2 x (dots, reduce, axpy),
+  // norm dots + reduce, Givens, next basis vector, advance
+  static constexpr int kIterationKernels = 14;
 
   template <class T>
   int alloc(T** p, size_t count) {
@@ -144,6 +156,16 @@ struct hobi_ctx {
   // --------------------------------------------------------------- matvec pipeline
   int farfield(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, double* out) {
     cudaEvent_t a = nullptr, bb = nullptr;
+    if (prof && capturing) {
+      const int pi = fp32 ? 1 : 0;
+      for (int q = 0; q < 2; ++q)
+        if (!gev[pi][q]) HOBI_CK(cudaEventCreate(&gev[pi][q]));
+      HOBI_CK(cudaEventRecordWithFlags(gev[pi][0], stream, cudaEventRecordExternal));
+      HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream));
+      HOBI_CK(cudaEventRecordWithFlags(gev[pi][1], stream, cudaEventRecordExternal));
+      graph_pairs[pi] = (double)p.n_targets * (double)n_nodes;
+      return HOBI_OK;
+    }
     if (prof) {
       if (prof_used == prof_ev.size()) {
         cudaEvent_t e0, e1;
@@ -172,6 +194,7 @@ struct hobi_ctx {
     HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part));
     HOBI_CK(launch_combine((int)nv, plan[fp32].chunks, part, F, inc_ptr, inc_face, corr, eps, u, kptr, ld, Au,
                            stream));
+    if (!capturing) launches += 3;
     return HOBI_OK;
   }
 
@@ -205,36 +228,57 @@ struct hobi_ctx {
     HOBI_CK(launch_givens(st, m, H, cs, sn, g, hcol, nrm, stream));
     HOBI_CK(launch_next_basis(Vb, n, w, n, st, stream));
     HOBI_CK(launch_advance(st, stream));
+    if (!capturing) launches += kIterationKernels - 3;
     return HOBI_OK;
   }
 
   int run_iteration() {
     const int pi = precision == HOBI_FP32_BULK;
-    if (!use_graph || prof) return iteration();
-    if (!graph[pi]) {
+    if (!use_graph || (prof && graph_timing_unavailable)) return iteration();
+    cudaGraphExec_t& gx = graph[pi][prof ? 1 : 0];
+    if (!gx) {
       cudaGraph_t gr = nullptr;
       HOBI_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      capturing = true;
       int r = iteration();
+      capturing = false;
       cudaError_t e = cudaStreamEndCapture(stream, &gr);
       if (r != HOBI_OK) {
         if (gr) cudaGraphDestroy(gr);
         return r;
       }
       if (e != cudaSuccess) return fail(HOBI_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&graph[pi], gr, 0);
+      e = cudaGraphInstantiate(&gx, gr, 0);
       cudaGraphDestroy(gr);
       if (e != cudaSuccess) {
-        graph[pi] = nullptr;
+        gx = nullptr;
         return fail(HOBI_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
       }
     }
-    HOBI_CK(cudaGraphLaunch(graph[pi], stream));
+    HOBI_CK(cudaGraphLaunch(gx, stream));
+    launches += kIterationKernels;
+    if (prof) {
+      replay_prof_pending = true;
+      replay_prof_pi = pi;
+    }
     return HOBI_OK;
   }
 
   int read_state() {
     HOBI_CK(cudaMemcpyAsync(st_host, st, sizeof(GmresState), cudaMemcpyDeviceToHost, stream));
     HOBI_CK(cudaStreamSynchronize(stream));
+    if (replay_prof_pending) {  // far-field time inside the graph that just completed
+      float ms = 0.f;
+      replay_prof_pending = false;
+      if (cudaEventElapsedTime(&ms, gev[replay_prof_pi][0], gev[replay_prof_pi][1]) != cudaSuccess) {
+        cudaGetLastError();
+        graph_timing_unavailable = true;  // later profiled iterations launch directly
+      } else {
+        prof_ms += ms;
+        prof_launches += 1;
+        prof_pairs += graph_pairs[replay_prof_pi];
+      }
+    }
     return HOBI_OK;
   }
 
@@ -266,13 +310,18 @@ struct hobi_ctx {
                           src64, stream));
     HOBI_TRY(farfield(fp32, p, t32, t64, ppart));
     HOBI_CK(launch_reduce_points((int)np, p.chunks, ppart, phi, stream));
+    launches += 3;
     return HOBI_OK;
   }
 
   ~hobi_ctx() {
     if (stream) cudaStreamSynchronize(stream);
-    for (auto& gexec : graph)
-      if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& row : graph)
+      for (auto& gexec : row)
+        if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& row : gev)
+      for (auto& ev : row)
+        if (ev) cudaEventDestroy(ev);
     for (void* p : allocs)
       if (p) cudaFree(p);
     for (auto& e : prof_ev) {
@@ -332,6 +381,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_CK(launch_validate((int)nv, (int)nf, (int)nc, h->V, h->Nin, h->F, h->inc_ptr, h->inc_face, h->Q, h->Nv,
                           h->vol_part, 256, h->center_part, h->flags, h->stream));
   HOBI_CK(launch_finish_validate((int)nv, h->vol_part, 256, h->center_part, h->center, h->flags, h->stream));
+  h->launches += 5 + 3 + (nc > 0 ? 1 : 0);  // adjacency (5), validation (3 + charges)
   int flags = 0;
   HOBI_CK(cudaMemcpyAsync(&flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HOBI_CK(cudaStreamSynchronize(h->stream));
@@ -360,6 +410,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_CK(launch_targets((int)nv, h->V, h->Nv, h->center, h->tgt32, h->tgt64, h->stream));
   HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
   HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
+  h->launches += 4 + (nc > 0 ? 1 : 0) + (h->n_pad > h->n_nodes ? 1 : 0);
 
   // far-field plans and partial-sum buffers
   size_t part_elems = 0;
@@ -549,6 +600,7 @@ int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, 
   HOBI_CK(launch_dots(nullptr, 0, h->Vb, n, h->st, 1, h->dpart, h->stream));
   HOBI_CK(launch_reduce_dots(h->dpart, m, h->st, 1, h->nrm, nullptr, 0, h->stream));
   HOBI_CK(launch_cycle_start(h->Vb, n, h->nrm, h->st, h->g, m, 1, h->stream));
+  h->launches += 3;
   HOBI_TRY(h->read_state());
   std::vector<double> hist;
   hist.push_back(h->st_host->rel);
@@ -562,6 +614,7 @@ int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, 
       if (h->st_host->converged || h->st_host->breakdown) break;
     }
     HOBI_CK(launch_finish_cycle(h->H, m, h->g, h->st, h->y, h->Vb, n, h->x, n, h->stream));
+    h->launches += 2;
     if (h->st_host->converged || h->st_host->breakdown || h->st_host->it >= max_it) break;
     // restart from r = b - A x
     HOBI_TRY(h->matvec_dev(h->x, nullptr, 0, h->w));
@@ -569,6 +622,7 @@ int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, 
     HOBI_CK(launch_dots(nullptr, 0, h->Vb, n, h->st, 1, h->dpart, h->stream));
     HOBI_CK(launch_reduce_dots(h->dpart, m, h->st, 1, h->nrm, nullptr, 0, h->stream));
     HOBI_CK(launch_cycle_start(h->Vb, n, h->nrm, h->st, h->g, m, 0, h->stream));
+    h->launches += 4;
     HOBI_TRY(h->read_state());
     done = h->st_host->converged || h->st_host->breakdown;
   }
@@ -629,6 +683,7 @@ int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, do
   HOBI_TRY(h->ensure_point_buffers(n_points));
   HOBI_TRY(h->copy_in(h->pts_in, points, 3 * n_points));
   HOBI_CK(launch_points((int)n_points, h->pts_in, 3, h->center, h->ptgt32, h->ptgt64, h->stream));
+  h->launches += 1;
   HOBI_TRY(h->reaction_dev(n_points, h->ptgt32, h->ptgt64, h->phi_pts));
   HOBI_TRY(h->copy_out(phi, h->phi_pts, n_points));
   HOBI_TRY(h->finish());
@@ -648,6 +703,7 @@ int hobi_energy(hobi_t h, double* e_sol) {
   HOBI_TRY(h->ensure_point_buffers(h->nc));
   HOBI_TRY(h->reaction_dev(h->nc, h->ctgt32, h->ctgt64, h->phi_pts));
   HOBI_CK(launch_energy_sum((int)h->nc, h->Q, h->phi_pts, h->e_dev, h->stream));
+  h->launches += 1;
   HOBI_CK(cudaMemcpyAsync(h->host_scalar, h->e_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   HOBI_TRY(h->leave());
   HOBI_CK(cudaStreamSynchronize(h->stream));
@@ -697,6 +753,12 @@ int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* 
   h->prof_ms = 0.0;
   h->prof_launches = 0;
   h->prof_pairs = 0.0;
+  return HOBI_OK;
+}
+
+int hobi_kernel_launches(hobi_t h, int64_t* n) {
+  if (!h || !n) return fail(HOBI_ERR_ARG, "NULL argument");
+  *n = h->launches;
   return HOBI_OK;
 }
 

@@ -33,8 +33,8 @@ KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
 EXPORTS = [
     "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
     "hobi_solve", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential", "hobi_energy",
-    "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_destroy",
-    "hobi_last_error",
+    "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches",
+    "hobi_destroy", "hobi_last_error",
 ]
 
 
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_get_correction.argtypes = [vp, C.POINTER(i64), dp, dp, dp]
     lib.hobi_profile_enable.argtypes = [vp, C.c_int32]
     lib.hobi_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(C.c_double)]
+    lib.hobi_kernel_launches.argtypes = [vp, C.POINTER(i64)]
     lib.hobi_destroy.argtypes = [vp]
     lib.hobi_destroy.restype = None
     lib.hobi_last_error.argtypes = []
@@ -105,6 +106,10 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+def _is_cuda_tensor(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
 class Solver:
     """One molecule on one GPU (wraps a hobi_t handle).
 
@@ -116,7 +121,7 @@ class Solver:
                  restart: int = 50, use_graph: bool = True, device: int | None = None, stream=None):
         lib = load_library()
         self._lib = lib
-        self.device_mode = _is_torch(V)
+        self.device_mode = _is_cuda_tensor(V)
         opt = Options()
         lib.hobi_default_options(C.byref(opt))
         opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
@@ -139,12 +144,17 @@ class Solver:
         else:
             opt.device = -1 if device is None else int(device)
             opt.mem_device = 0
-            self._keep = [np.ascontiguousarray(V, dtype=np.float64), np.ascontiguousarray(F, dtype=np.int32),
-                          np.ascontiguousarray(N, dtype=np.float64),
-                          np.ascontiguousarray(charges, dtype=np.float64).reshape(-1, 4)]
-            Va, Fa, Na, Qa = self._keep
-            ptrs = [Va.ctypes.data, Fa.ctypes.data, Na.ctypes.data, Qa.ctypes.data if Qa.size else None]
-            nv, nf, nc = Va.shape[0], Fa.shape[0], Qa.shape[0]
+            if _is_torch(V):  # host torch tensors (e.g. pinned buffers): pass their host pointers
+                self._keep = [t.contiguous() for t in (V, F, N, charges)]
+                ptrs = [t.data_ptr() if t.numel() else None for t in self._keep]
+                nv, nf, nc = self._keep[0].shape[0], self._keep[1].shape[0], self._keep[3].reshape(-1, 4).shape[0]
+            else:
+                self._keep = [np.ascontiguousarray(V, dtype=np.float64), np.ascontiguousarray(F, dtype=np.int32),
+                              np.ascontiguousarray(N, dtype=np.float64),
+                              np.ascontiguousarray(charges, dtype=np.float64).reshape(-1, 4)]
+                Va, Fa, Na, Qa = self._keep
+                ptrs = [Va.ctypes.data, Fa.ctypes.data, Na.ctypes.data, Qa.ctypes.data if Qa.size else None]
+                nv, nf, nc = Va.shape[0], Fa.shape[0], Qa.shape[0]
         h = C.c_void_p()
         _check(lib.hobi_setup(ptrs[0], nv, ptrs[1], nf, ptrs[2], ptrs[3], nc, float(eps1), float(eps2),
                               float(kappa), C.byref(opt), C.byref(h)))
@@ -261,6 +271,11 @@ class Solver:
         c = np.empty((ne, 3, 4), dtype=np.float64)
         _check(self._lib.hobi_get_correction(self._h, C.byref(n), v.ctypes.data, f.ctypes.data, c.ctypes.data))
         return v, f, c
+
+    def kernel_launches(self) -> int:
+        n = C.c_int64()
+        _check(self._lib.hobi_kernel_launches(self._h, C.byref(n)))
+        return int(n.value)
 
     def profile_enable(self, on: bool = True):
         _check(self._lib.hobi_profile_enable(self._h, 1 if on else 0))

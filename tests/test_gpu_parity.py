@@ -283,3 +283,23 @@ def test_kirkwood_c2_level5_fp32_vs_fp64():
     e_ex = kw.solvation_energy(Q, 10.0, 1.0, 80.0, 0.1257)
     assert np.max(np.abs(p64 - phi_ex)) / np.max(np.abs(phi_ex)) < 2e-3
     assert abs(e64 - e_ex) / abs(e_ex) < 2e-3
+
+
+def test_profiling_counts_farfield_launches_with_graphs(problems):
+    """Far-field timing via event nodes inside the captured graph: one launch per iteration
+    (plus the energy launch), results identical to an unprofiled solve."""
+    p = problems["c2_l4"]
+    a = _solver(p, "fp32")
+    b = _solver(p, "fp32")
+    b.profile_enable(True)
+    pa, da, ia = a.solve(1e-6)
+    pb, db, ib = b.solve(1e-6)
+    assert np.array_equal(pa, pb) and np.array_equal(da, db)
+    b.energy()
+    prof = b.profile_read()
+    # every far-field launch timed (graph event nodes, or direct launches where those cannot be
+    # timed -- the first replay is then lost to the switch)
+    assert ib["iterations"] <= prof["launches"] <= ib["iterations"] + 1
+    assert prof["farfield_ms"] > 0
+    assert prof["pairs"] == (prof["launches"] - 1) * b.nv * b.n_nodes + b.nc * b.n_nodes
+    assert b.kernel_launches() > 14 * ib["iterations"]
