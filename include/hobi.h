@@ -136,6 +136,22 @@ int hobi_get_solution(hobi_t h, double* u);
  * points [n_points][3], phi [n_points] (formulation units). */
 int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, double* phi);
 
+/* Same result as hobi_reaction_potential, but the call allocates no device memory. The paper
+ * has no counterpart: this entry point serves callers that cannot allocate at call time (code
+ * running while a stream is captured into a CUDA graph, code that must avoid the device-wide
+ * synchronisation an allocation can cause, hosts whose device memory belongs to another
+ * allocator). Create the handle (hobi_setup) beforehand; this call then uses the handle's
+ * tables plus one file-scope device array of 2.5 MiB that every GPU loading the library keeps
+ * until process exit.
+ *   n_points <= 4096 per call; larger requests return HOBI_ERR_ARG (split them, or use
+ *   hobi_reaction_potential). points/phi follow opt.mem_device like every array argument.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture.
+ *   The array is shared by every call on a device and keeps the last call's contents: calls
+ *   that overlap on the GPU (different streams or handles on one device) race on it.
+ * Results equal hobi_reaction_potential's up to summation order (at most 64 source chunks). */
+int hobi_reaction_potential_noalloc(hobi_t h, const double* points, int64_t n_points, double* phi);
+
 /* Electrostatic solvation energy E_sol = (1/2) sum_k q_k phi_reac(x_k) in kcal/mol
  * (Eq. solvation_energy) from the handle's solution; requires hobi_solve or
  * hobi_set_solution first (else HOBI_ERR_STATE). e_sol is a host pointer. */

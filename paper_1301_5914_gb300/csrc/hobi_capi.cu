@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -769,3 +770,88 @@ void hobi_destroy(hobi_t h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Reaction potential without any device allocation.
+//
+// For callers that cannot allocate device memory at call time: code that runs while a CUDA
+// stream is being captured into a graph (cudaMalloc is not allowed there), code that must not
+// trigger the device-wide synchronisation an allocation can cause, or hosts whose device memory
+// is owned by another allocator. The per-call scratch (the caller's points as targets, the
+// per-chunk partial sums and the reduced potentials) lives in one file-scope device array of
+// fixed size instead of buffers allocated on demand; the handle's own tables were allocated by
+// hobi_setup beforehand.
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = 4096;  // points per call
+constexpr int kNoAllocMaxChunks = 64;        // source chunks of the far-field sum
+// layout: points [3n] double | targets64 [8n] double | phi [n] double | partials [64 n] double |
+//         targets32 [2n] float4
+constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxPoints * (3 + 8 + 1 + kNoAllocMaxChunks) * sizeof(double) +
+                                 (size_t)kNoAllocMaxPoints * 2 * sizeof(float4);
+
+}  // namespace
+
+// 2.5 MiB, shared by every call on a device; resident on every GPU that loads the library.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (current device). Looked up once per device:
+// in host code the array's name is only a host-side stand-in, not a device address.
+int noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(HOBI_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HOBI_ERR_CUDA, std::string("cudaGetSymbolAddress(no-allocation scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return HOBI_OK;
+}
+
+}  // namespace
+
+extern "C" int hobi_reaction_potential_noalloc(hobi_t h, const double* points, int64_t n_points, double* phi) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (n_points < 0 || (n_points > 0 && (!points || !phi))) return fail(HOBI_ERR_ARG, "bad points/phi arguments");
+  if (n_points > kNoAllocMaxPoints)
+    return fail(HOBI_ERR_ARG, "n_points = " + std::to_string(n_points) + " exceeds the no-allocation limit of " +
+                                  std::to_string(kNoAllocMaxPoints) + " points per call");
+  if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
+  if (n_points == 0) return HOBI_OK;
+  DeviceGuard guard(h->device);
+  unsigned char* base = nullptr;
+  HOBI_TRY(noalloc_scratch(h->device, &base));
+  const int64_t n = n_points;
+  double* pts = reinterpret_cast<double*>(base);
+  double* t64 = pts + 3 * kNoAllocMaxPoints;
+  double* phi_d = t64 + 8 * kNoAllocMaxPoints;
+  double* part = phi_d + kNoAllocMaxPoints;
+  float4* t32 = reinterpret_cast<float4*>(part + (size_t)kNoAllocMaxChunks * kNoAllocMaxPoints);
+  const bool fp32 = h->precision == HOBI_FP32_BULK;
+  FarFieldPlan p = plan_farfield(fp32, (int)n, (int)h->n_pad, false, h->num_sms, farfield_blocks_per_sm(fp32, false));
+  if (p.chunks > kNoAllocMaxChunks) {
+    p.tiles_per_chunk = (p.n_tiles + kNoAllocMaxChunks - 1) / kNoAllocMaxChunks;
+    p.chunks = (p.n_tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+  }
+  // every (chunk, point) partial is written by the far-field kernel before it is read, so the
+  // scratch left over from an earlier call needs no clearing
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->copy_in(pts, points, 3 * n));
+  HOBI_CK(launch_points((int)n, pts, 3, h->center, t32, t64, h->stream));
+  HOBI_CK(launch_gather(fp32, (int)h->n_nodes, (int)h->n_pad, (int)h->nv, h->F, h->ny, h->nnu, h->nW, h->center,
+                        h->x, nullptr, 0, h->src32, h->src64, h->stream));
+  HOBI_CK(launch_farfield(fp32, p, t32, t64, h->src32, h->src64, h->eps, h->kappa, part, h->stream));
+  HOBI_CK(launch_reduce_points((int)n, p.chunks, part, phi_d, h->stream));
+  h->launches += 4;
+  HOBI_TRY(h->copy_out(phi, phi_d, n));
+  return h->finish();
+}

@@ -32,7 +32,8 @@ KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
 
 EXPORTS = [
     "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
-    "hobi_solve", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential", "hobi_energy",
+    "hobi_solve", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
+    "hobi_reaction_potential_noalloc", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches",
     "hobi_destroy", "hobi_last_error",
 ]
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_set_solution.argtypes = [vp, dp]
     lib.hobi_get_solution.argtypes = [vp, dp]
     lib.hobi_reaction_potential.argtypes = [vp, dp, i64, dp]
+    lib.hobi_reaction_potential_noalloc.argtypes = [vp, dp, i64, dp]
     lib.hobi_energy.argtypes = [vp, C.POINTER(C.c_double)]
     lib.hobi_get_nodes.argtypes = [vp, dp, dp, dp]
     lib.hobi_get_correction.argtypes = [vp, C.POINTER(i64), dp, dp, dp]
