@@ -51,7 +51,7 @@ WORKLOAD = {
 }
 OPS_PER_PAIR = 36  # FP32 FMA-pipe instructions per pair in the both-rows far-field kernel
 MUFU_PER_PAIR = 2  # rsqrt.approx + ex2.approx
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "farfield32_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "farfield32_c2_ico6_traffic.txt")
 FARFIELD_SRC = os.path.join(ROOT, "paper_1301_5914_gb300", "csrc", "k_farfield.cu")
 
 
@@ -126,13 +126,17 @@ class ClockSampler:
 
 
 def _traffic_per_launch():
-    """DRAM bytes per far-field launch from the committed ncu capture, if the kernel source is unchanged."""
+    """DRAM bytes per far-field launch from the committed ncu summary, if the kernel source is unchanged."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        rec = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
         h = hashlib.sha256(open(FARFIELD_SRC, "rb").read()).hexdigest()
         if rec.get("kernel_source_sha256") == h:
-            return rec.get("dram_bytes_per_launch_full_size")
-    except (OSError, ValueError):
+            return int(rec["dram_bytes_per_launch_full_size"])
+    except (OSError, ValueError, KeyError):
         pass
     return None
 
