@@ -190,8 +190,8 @@ struct hobi_ctx {
   // Au = A u with u = base + (*kptr) * ld when kptr is given (device pointers)
   int matvec_dev(const double* u, const int* kptr, int64_t ld, double* Au) {
     const bool fp32 = precision == HOBI_FP32_BULK;
-    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, src32,
-                          src64, stream));
+    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps,
+                          src32, src64, stream));
     HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part));
     HOBI_CK(launch_combine((int)nv, plan[fp32].chunks, part, F, inc_ptr, inc_face, corr, eps, u, kptr, ld, Au,
                            stream));
@@ -307,8 +307,8 @@ struct hobi_ctx {
     const bool fp32 = precision == HOBI_FP32_BULK;
     FarFieldPlan p = plan_farfield(fp32, (int)np, (int)n_pad, false, num_sms, farfield_blocks_per_sm(fp32, false));
     HOBI_TRY(ensure_ppart((size_t)p.chunks * (size_t)np));
-    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, x, nullptr, 0, src32,
-                          src64, stream));
+    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, x, nullptr, 0, 1.0 / eps,
+                          src32, src64, stream));
     HOBI_TRY(farfield(fp32, p, t32, t64, ppart));
     HOBI_CK(launch_reduce_points((int)np, p.chunks, ppart, phi, stream));
     launches += 3;
@@ -402,7 +402,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_TRY(h->alloc(&h->tgt64, 8 * nv));
   HOBI_TRY(h->alloc(&h->ctgt32, 2 * (nc > 0 ? nc : 1)));
   HOBI_TRY(h->alloc(&h->ctgt64, 8 * (nc > 0 ? nc : 1)));
-  HOBI_TRY(h->alloc(&h->src32, 2 * h->n_pad));
+  HOBI_TRY(h->alloc(&h->src32, 4 * h->n_pad));
   HOBI_TRY(h->alloc(&h->src64, 8 * h->n_pad));
   HOBI_CK(launch_node_gen((int)nf, h->F, h->V, h->Nv, h->center, h->elem, h->ny, h->nnu, h->nW, h->stream));
   HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem, h->ny,
@@ -848,7 +848,7 @@ extern "C" int hobi_reaction_potential_noalloc(hobi_t h, const double* points, i
   HOBI_TRY(h->copy_in(pts, points, 3 * n));
   HOBI_CK(launch_points((int)n, pts, 3, h->center, t32, t64, h->stream));
   HOBI_CK(launch_gather(fp32, (int)h->n_nodes, (int)h->n_pad, (int)h->nv, h->F, h->ny, h->nnu, h->nW, h->center,
-                        h->x, nullptr, 0, h->src32, h->src64, h->stream));
+                        h->x, nullptr, 0, 1.0 / h->eps, h->src32, h->src64, h->stream));
   HOBI_CK(launch_farfield(fp32, p, t32, t64, h->src32, h->src64, h->eps, h->kappa, part, h->stream));
   HOBI_CK(launch_reduce_points((int)n, p.chunks, part, phi_d, h->stream));
   h->launches += 4;

@@ -8,7 +8,8 @@
 //   inc_ptr[n_v+1], inc_face[3 n_f]                            vertex -> incident faces (sorted)
 //   corr[3 n_f][3][4]         singular correction per (vertex, incident face) entry (FP64)
 //   tgt32[n_v][2] float4      target x - c and unit normal (FP32 path)
-//   src32[n_pad][2] float4    (y - c, sigma/4pi), (mu nu_y/4pi, 0) per node, rebuilt per matvec
+//   src32[n_pad][4] float4    per node, each value twice for paired FP32 math, rebuilt per matvec:
+//                             {-y}, {sigma}, {m = mu nu_y}, {sigma/eps} (y relative to c; sigma, mu / 4pi)
 //   src64[n_pad][8] double    (y - c, sigma/4pi, mu nu_y/4pi, 0) per node (FP64 path)
 //   part[chunks][2 n_v]       FP64 far-field partial sums per source chunk
 // c is the vertex centroid: both precisions work in coordinates relative to it.
@@ -72,7 +73,8 @@ cudaError_t launch_points(int np, const double* P, int stride, const double* cen
 // If kptr != nullptr the vector is u + (*kptr) * ld (GMRES basis column).
 cudaError_t launch_gather(bool fp32, int n_nodes, int n_pad, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
-                          const int* kptr, int64_t ld, float4* src32, double* src64, cudaStream_t s);
+                          const int* kptr, int64_t ld, double inv_eps, float4* src32, double* src64,
+                          cudaStream_t s);
 cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* src64, cudaStream_t s);
 
 struct FarFieldPlan {

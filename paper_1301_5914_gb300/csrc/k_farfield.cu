@@ -13,9 +13,12 @@
 // accumulation instead of two dot products. Faces incident to x_i are included here and
 // replaced by the singular rule through the precomputed correction (combine kernel).
 //
-// FP32-bulk kernel: each thread keeps 4 targets in registers; 256-node source tiles are staged
-// in shared memory and read as warp-wide broadcasts; rsqrt and exp2 go to the MUFU pipe
-// (rsqrt.approx / ex2.approx), everything else is FP32 FMA-pipe work (36 instructions a pair).
+// FP32-bulk kernel: each thread keeps 4 targets in registers as two packed pairs and evaluates
+// every pair formula with Blackwell's paired FP32 instructions (__ffma2_rn / __fmul2_rn /
+// __fadd2_rn: one instruction = the same operation on two targets), which halves the issue
+// slots of the FMA-pipe work so that the FMA pipe itself becomes the limit. 256-node source
+// tiles are staged in shared memory, each source value stored twice ({v, v}) so one LDS.128
+// feeds two packed operands; rsqrt and exp2 go to the MUFU pipe (rsqrt.approx / ex2.approx).
 // Each tile's FP32 sum is folded into a compensated (two-float) accumulator, and the result is
 // written as FP64 per (source chunk, target); the combine kernel adds the chunks in a fixed order.
 #include <math.h>
@@ -48,7 +51,7 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 __global__ void k_gather32(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
                            const double* __restrict__ nnu, const double* __restrict__ nW,
                            const double* __restrict__ center, const double* __restrict__ u, const int* kptr,
-                           int64_t ld, float4* __restrict__ src) {
+                           int64_t ld, double inv_eps, float4* __restrict__ src) {
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= n_nodes) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
@@ -59,9 +62,15 @@ __global__ void k_gather32(int n_nodes, int nv, const int* __restrict__ F, const
   double mu = (W[0] * u[a] + W[1] * u[b] + W[2] * u[c]) * kInv4Pi;
   const double* y = ny + 3 * (size_t)node;
   const double* n = nnu + 3 * (size_t)node;
-  src[2 * (size_t)node] = make_float4((float)(y[0] - center[0]), (float)(y[1] - center[1]),
-                                      (float)(y[2] - center[2]), (float)sig);
-  src[2 * (size_t)node + 1] = make_float4((float)(mu * n[0]), (float)(mu * n[1]), (float)(mu * n[2]), 0.f);
+  // {-y_x, -y_x, -y_y, -y_y}, {-y_z, -y_z, sigma, sigma}, {m_x, m_x, m_y, m_y}, {m_z, m_z, sigma/eps, sigma/eps}
+  const float yx = (float)(center[0] - y[0]), yy = (float)(center[1] - y[1]), yz = (float)(center[2] - y[2]);
+  const float sg = (float)sig, se = (float)(sig * inv_eps);
+  const float mx = (float)(mu * n[0]), my = (float)(mu * n[1]), mz = (float)(mu * n[2]);
+  float4* o = src + 4 * (size_t)node;
+  o[0] = make_float4(yx, yx, yy, yy);
+  o[1] = make_float4(yz, yz, sg, sg);
+  o[2] = make_float4(mx, mx, my, my);
+  o[3] = make_float4(mz, mz, se, se);
 }
 
 __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
@@ -93,74 +102,97 @@ __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const
 __global__ void k_pad(int n_nodes, int n_pad, float4* src32, double* src64) {
   int node = n_nodes + blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= n_pad) return;
-  src32[2 * (size_t)node] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
-  src32[2 * (size_t)node + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  src32[4 * (size_t)node] = make_float4(-1.0e4f, -1.0e4f, -1.0e4f, -1.0e4f);
+  src32[4 * (size_t)node + 1] = make_float4(-1.0e4f, -1.0e4f, 0.f, 0.f);
+  src32[4 * (size_t)node + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+  src32[4 * (size_t)node + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
   double* o = src64 + 8 * (size_t)node;
   o[0] = o[1] = o[2] = 1.0e4;
   o[3] = o[4] = o[5] = o[6] = o[7] = 0.0;
 }
 
 // ------------------------------------------------------------------ far field, FP32 bulk
+__device__ __forceinline__ float2 pair_of(float a) { return make_float2(a, a); }
+
 template <bool ROW2>
 __global__ void __launch_bounds__(kFF32Threads, 2)
     k_farfield32(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src, int n_tiles, int tpc,
-                 float neg_kl2e, float kap, float eps, float ieps, double* __restrict__ part, int64_t ldp) {
-  constexpr int T = kFF32Targets, NT = kFF32Threads;
-  __shared__ float4 sh[2 * kTile];
-  float px[T], py[T], pz[T], qx[T], qy[T], qz[T];
+                 float neg_kl2e, float kap, float eps, double* __restrict__ part, int64_t ldp) {
+  constexpr int T = kFF32Targets, TP = kFF32Targets / 2, NT = kFF32Threads;
+  __shared__ float4 sh[4 * kTile];
+  float2 px[TP], py[TP], pz[TP];  // target k = 2p + lane
+  float qx[T], qy[T], qz[T];
   float h1[T], l1[T], h2[T], l2[T];
   const int base = blockIdx.x * (NT * T) + threadIdx.x;
 #pragma unroll
   for (int k = 0; k < T; ++k) {
     int i = min(base + k * NT, nt - 1);
     float4 a = tgt[2 * (size_t)i], b = tgt[2 * (size_t)i + 1];
-    px[k] = a.x; py[k] = a.y; pz[k] = a.z;
+    if (k & 1) {
+      px[k >> 1].y = a.x; py[k >> 1].y = a.y; pz[k >> 1].y = a.z;
+    } else {
+      px[k >> 1].x = a.x; py[k >> 1].x = a.y; pz[k >> 1].x = a.z;
+    }
     qx[k] = b.x; qy[k] = b.y; qz[k] = b.z;
     h1[k] = l1[k] = h2[k] = l2[k] = 0.f;
   }
+  const float2 nk2 = pair_of(neg_kl2e), kap2 = pair_of(kap), eps2 = pair_of(eps);
+  const float2 m1 = pair_of(-1.f), three = pair_of(3.f), m3 = pair_of(-3.f);
   const int t0 = blockIdx.y * tpc;
   const int t1 = min(n_tiles, t0 + tpc);
   for (int tile = t0; tile < t1; ++tile) {
     __syncthreads();
-    const float4* g = src + (size_t)tile * (2 * kTile);
-    for (int q = threadIdx.x; q < 2 * kTile; q += NT) sh[q] = g[q];
+    const float4* g = src + (size_t)tile * (4 * kTile);
+    for (int q = threadIdx.x; q < 4 * kTile; q += NT) sh[q] = g[q];
     __syncthreads();
-    float a1[T], wx[T], wy[T], wz[T];
+    float2 a1[TP], wx[TP], wy[TP], wz[TP];
 #pragma unroll
-    for (int k = 0; k < T; ++k) a1[k] = wx[k] = wy[k] = wz[k] = 0.f;
+    for (int k = 0; k < TP; ++k) a1[k] = wx[k] = wy[k] = wz[k] = pair_of(0.f);
 #pragma unroll 2
     for (int s = 0; s < kTile; ++s) {
-      const float4 p = sh[2 * s];
-      const float4 m = sh[2 * s + 1];
+      const float4 A = sh[4 * s], B = sh[4 * s + 1], C = sh[4 * s + 2], D = sh[4 * s + 3];
+      const float2 nyx = make_float2(A.x, A.y), nyy = make_float2(A.z, A.w), nyz = make_float2(B.x, B.y);
+      const float2 sg = make_float2(B.z, B.w), mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w);
+      const float2 mz = make_float2(D.x, D.y), se = make_float2(D.z, D.w);
 #pragma unroll
-      for (int k = 0; k < T; ++k) {
-        float dx = px[k] - p.x, dy = py[k] - p.y, dz = pz[k] - p.z;
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float ir = rsqrt_approx(r2);
-        float r = r2 * ir;
-        float E = exp2_approx(neg_kl2e * r);
-        float aym = fmaf(dx, m.x, fmaf(dy, m.y, dz * m.z));
-        float ir2 = ir * ir;
-        float ir3 = ir2 * ir;
-        float kr = kap * r;
-        float P = fmaf(E, kr, E);
-        a1[k] = fmaf(fmaf(-E, ir, ir), p.w, a1[k]);
-        a1[k] = fmaf(fmaf(eps, P, -1.f) * ir3, aym, a1[k]);
+      for (int k = 0; k < TP; ++k) {
+        const float2 dx = __fadd2_rn(px[k], nyx), dy = __fadd2_rn(py[k], nyy), dz = __fadd2_rn(pz[k], nyz);
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 r = __fmul2_rn(r2, ir);
+        const float2 ea = __fmul2_rn(nk2, r);
+        const float2 E = make_float2(exp2_approx(ea.x), exp2_approx(ea.y));
+        const float2 aym = __ffma2_rn(dz, mz, __ffma2_rn(dy, my, __fmul2_rn(dx, mx)));  // d . m
+        const float2 ir2 = __fmul2_rn(ir, ir);
+        const float2 ir3 = __fmul2_rn(ir2, ir);
+        const float2 u3 = __fmul2_rn(aym, ir3);                                       // (d . m)/r^3
+        const float2 kr = __fmul2_rn(kap2, r);
+        const float2 P = __ffma2_rn(E, kr, E);
+        // row 1: (1 - E)/r sigma + (eps P - 1)(d . m)/r^3
+        a1[k] = __ffma2_rn(__ffma2_rn(make_float2(-E.x, -E.y), ir, ir), sg, a1[k]);
+        a1[k] = __ffma2_rn(__ffma2_rn(eps2, P, m1), u3, a1[k]);
         if (ROW2) {
-          float Q3 = fmaf(E, fmaf(kr, kr + 3.f, 3.f), -3.f);
-          float ir5 = ir3 * ir2;
-          float w = fmaf(P, ir3, -ir3);
-          float sv = fmaf(-Q3 * ir5, aym, fmaf(P, ieps, -1.f) * ir3 * p.w);
-          wx[k] = fmaf(w, m.x, fmaf(sv, dx, wx[k]));
-          wy[k] = fmaf(w, m.y, fmaf(sv, dy, wy[k]));
-          wz[k] = fmaf(w, m.z, fmaf(sv, dz, wz[k]));
+          const float2 Q3 = __ffma2_rn(E, __ffma2_rn(kr, __fadd2_rn(kr, three), three), m3);  // Q - 3
+          const float2 w = __ffma2_rn(P, ir3, make_float2(-ir3.x, -ir3.y));                  // (P - 1)/r^3
+          const float2 q2 = __fmul2_rn(Q3, ir2);
+          // (P/eps - 1) sigma / r^3 - (Q - 3)(d . m)/r^5
+          const float2 sv = __ffma2_rn(make_float2(-q2.x, -q2.y), u3,
+                                       __fmul2_rn(__ffma2_rn(P, se, make_float2(-sg.x, -sg.y)), ir3));
+          wx[k] = __ffma2_rn(w, mx, __ffma2_rn(sv, dx, wx[k]));
+          wy[k] = __ffma2_rn(w, my, __ffma2_rn(sv, dy, wy[k]));
+          wz[k] = __ffma2_rn(w, mz, __ffma2_rn(sv, dz, wz[k]));
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < T; ++k) {
-      two_sum_acc(h1[k], l1[k], a1[k]);
-      if (ROW2) two_sum_acc(h2[k], l2[k], fmaf(qx[k], wx[k], fmaf(qy[k], wy[k], qz[k] * wz[k])));
+    for (int k = 0; k < TP; ++k) {
+      two_sum_acc(h1[2 * k], l1[2 * k], a1[k].x);
+      two_sum_acc(h1[2 * k + 1], l1[2 * k + 1], a1[k].y);
+      if (ROW2) {
+        two_sum_acc(h2[2 * k], l2[2 * k], fmaf(qx[2 * k], wx[k].x, fmaf(qy[2 * k], wy[k].x, qz[2 * k] * wz[k].x)));
+        two_sum_acc(h2[2 * k + 1], l2[2 * k + 1],
+                    fmaf(qx[2 * k + 1], wx[k].y, fmaf(qy[2 * k + 1], wy[k].y, qz[2 * k + 1] * wz[k].y)));
+      }
     }
   }
   double* out = part + (size_t)blockIdx.y * ldp;
@@ -290,10 +322,11 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 cudaError_t launch_gather(bool fp32, int n_nodes, int n_pad, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
-                          const int* kptr, int64_t ld, float4* src32, double* src64, cudaStream_t s) {
+                          const int* kptr, int64_t ld, double inv_eps, float4* src32, double* src64,
+                          cudaStream_t s) {
   (void)n_pad;
   if (fp32)
-    k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, src32);
+    k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, src32);
   else
     k_gather64<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, src64);
   return cudaGetLastError();
@@ -359,12 +392,10 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
     const float neg_kl2e = (float)(-kappa * 1.4426950408889634074);
     if (p.row2)
       k_farfield32<true><<<grid, kFF32Threads, 0, s>>>(tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk,
-                                                       neg_kl2e, (float)kappa, (float)eps, (float)(1.0 / eps),
-                                                       part, ldp);
+                                                       neg_kl2e, (float)kappa, (float)eps, part, ldp);
     else
       k_farfield32<false><<<grid, kFF32Threads, 0, s>>>(tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk,
-                                                        neg_kl2e, (float)kappa, (float)eps, (float)(1.0 / eps),
-                                                        part, ldp);
+                                                        neg_kl2e, (float)kappa, (float)eps, part, ldp);
   } else {
     dim3 grid((p.n_targets + kFF64Threads * kFF64Targets - 1) / (kFF64Threads * kFF64Targets), p.chunks);
     if (p.row2)
