@@ -404,7 +404,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_TRY(h->alloc(&h->ctgt64, 8 * (nc > 0 ? nc : 1)));
   HOBI_TRY(h->alloc(&h->src32, 4 * h->n_pad));
   HOBI_TRY(h->alloc(&h->src64, 8 * h->n_pad));
-  HOBI_CK(launch_node_gen((int)nf, h->F, h->V, h->Nv, h->center, h->elem, h->ny, h->nnu, h->nW, h->stream));
+  HOBI_CK(launch_node_gen((int)nf, h->F, h->V, h->Nv, h->elem, h->ny, h->nnu, h->nW, h->flags, h->stream));
   HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem, h->ny,
                                     h->nnu, h->nW, h->eps, h->kappa, h->corr, h->stream));
   HOBI_CK(launch_rhs((int)nv, (int)nc, h->V, h->Nv, h->Q, h->eps1, h->b, h->stream));
@@ -412,6 +412,11 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
   HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
   h->launches += 4 + (nc > 0 ? 1 : 0) + (h->n_pad > h->n_nodes ? 1 : 0);
+  HOBI_CK(cudaMemcpyAsync(&flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  HOBI_CK(cudaStreamSynchronize(h->stream));
+  if (flags & kDegenerateElement)
+    return fail(HOBI_ERR_MESH, "invalid mesh: a curved element has a zero or non-finite area Jacobian "
+                               "(vertex normals inconsistent with the faces)");
 
   // far-field plans and partial-sum buffers
   size_t part_elems = 0;

@@ -42,6 +42,7 @@ enum MeshFlag : int {
   kNegativeVolume = 32,
   kDegenerateFace = 64,
   kBadCharge = 128,
+  kDegenerateElement = 256,
 };
 
 // ---- setup kernels (k_setup.cu) ----
@@ -54,8 +55,9 @@ cudaError_t launch_validate(int nv, int nf, int nc, const double* V, const doubl
                             cudaStream_t s);
 cudaError_t launch_finish_validate(int nv, const double* vol_part, int vol_blocks, const double* center_part,
                                    double* center, int* flags, cudaStream_t s);
-cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double* Nv, const double* center,
-                            double* elem, double* ny, double* nnu, double* nW, cudaStream_t s);
+// sets kDegenerateElement in *flags if a quadrature node's Jacobian is zero or not finite
+cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double* Nv, double* elem, double* ny,
+                            double* nnu, double* nW, int* flags, cudaStream_t s);
 // one thread per (vertex, incident face) entry; vert[e] is the entry's vertex
 cudaError_t launch_correction_entries(int n_entries, const int* vert, const int* F, const double* V,
                                       const double* Nv, const int* inc_face, const double* elem, const double* ny,

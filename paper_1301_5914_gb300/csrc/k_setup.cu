@@ -300,7 +300,7 @@ __device__ void gl4_point(int k, double* x, double* w) {
 }
 
 __global__ void k_node_gen(int nf, const int* F, const double* V, const double* Nv, double* elem, double* ny,
-                           double* nnu, double* nW) {
+                           double* nnu, double* nW, int* flags) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nf) return;
   int a = F[3 * j], b = F[3 * j + 1], c = F[3 * j + 2];
@@ -315,6 +315,7 @@ __global__ void k_node_gen(int nf, const int* F, const double* V, const double* 
     interpolate(p, r, s, &x, &xr, &xs);
     double3 cr = cross(xr, xs);
     double J = sqrt(dot(cr, cr));
+    if (!(J > 0.0) || !isfinite(J) || !isfinite(x.x + x.y + x.z)) atomicOr(flags, kDegenerateElement);
     size_t node = 4 * (size_t)j + m;
     st3(ny + 3 * node, x);
     st3(nnu + 3 * node, (1.0 / J) * cr);
@@ -486,10 +487,9 @@ cudaError_t launch_finish_validate(int nv, const double* vol_part, int vol_block
   return cudaGetLastError();
 }
 
-cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double* Nv, const double* center,
-                            double* elem, double* ny, double* nnu, double* nW, cudaStream_t s) {
-  (void)center;
-  k_node_gen<<<nblk(nf, 128), 128, 0, s>>>(nf, F, V, Nv, elem, ny, nnu, nW);
+cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double* Nv, double* elem, double* ny,
+                            double* nnu, double* nW, int* flags, cudaStream_t s) {
+  k_node_gen<<<nblk(nf, 128), 128, 0, s>>>(nf, F, V, Nv, elem, ny, nnu, nW, flags);
   return cudaGetLastError();
 }
 

@@ -135,29 +135,48 @@ def ball_charges(n: int, r_max: float, seed: int, center=(0.0, 0.0, 0.0)) -> np.
 # Synthetic molecules (stand-in for the paper's MSMS surfaces of 1ajj)
 # ---------------------------------------------------------------------------
 
-_BETA = 2.0  # Gaussian density sharpness: rho = sum exp(-beta (|x-c|^2/R^2 - 1))
+_BETA = 1.0  # Gaussian density sharpness: rho = sum exp(-beta (|x-c|^2/R^2 - 1))
+_PROBE = 0.6  # radius inflation (A) that closes most inter-atom tunnels, like a solvent probe
+_CUT2 = 20.0  # density terms beyond |x-c| = 4.47 R are dropped (exp(-19) relative)
 
 
 def _place_atoms(n_atoms: int, ball_radius: float, rng) -> tuple[np.ndarray, np.ndarray]:
-    """Sequential random packing: reject a candidate closer than 0.8 (Ri + Rj)."""
+    """Sequential random packing: reject a candidate closer than 0.8 (Ri + Rj) to a placed atom."""
     centers = np.empty((n_atoms, 3))
     radii = np.empty(n_atoms)
+    cell = 3.2  # >= 0.8 * (2.0 + 2.0): neighbours of a candidate sit in the 27 surrounding cells
+    grid: dict = {}
     k = 0
     tries = 0
     while k < n_atoms:
         tries += 1
-        if tries > 2000 * n_atoms:
+        if tries > 5000 * n_atoms:
             raise RuntimeError("atom packing failed; ball too small")
         c = rng.uniform(-ball_radius, ball_radius, 3)
         if c @ c > ball_radius * ball_radius:
             continue
         rad = rng.uniform(1.2, 2.0)
-        if k:
-            d2 = np.sum((centers[:k] - c) ** 2, axis=1)
-            if np.any(d2 < (0.8 * (radii[:k] + rad)) ** 2):
-                continue
+        key = tuple(np.floor(c / cell).astype(int))
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for idx in grid.get((key[0] + dx, key[1] + dy, key[2] + dz), ()):
+                        d = centers[idx] - c
+                        if d @ d < (0.8 * (radii[idx] + rad)) ** 2:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            continue
         centers[k] = c
         radii[k] = rad
+        grid.setdefault(key, []).append(k)
         k += 1
     return centers, radii
 
@@ -172,21 +191,42 @@ def _charges_for(centers: np.ndarray, rng) -> np.ndarray:
     return out
 
 
-def _density(points: np.ndarray, centers: np.ndarray, radii: np.ndarray, cutoff: float = 4.0):
-    """rho(x) and grad rho(x) at the given points (dense loops over atoms)."""
-    rho = np.zeros(points.shape[0])
-    grad = np.zeros_like(points)
-    inv_r2 = 1.0 / radii**2
+def _density_grid(centers, radii, lo, shape, h):
+    """rho - 1 on the grid lo + h*(i,j,k), each atom adding only inside its cutoff box."""
+    rho = np.zeros(shape)
     for a in range(centers.shape[0]):
-        d = points - centers[a]
-        t = np.einsum("ij,ij->i", d, d) * inv_r2[a]
-        m = t < cutoff * cutoff
-        if not np.any(m):
-            continue
-        g = np.exp(-_BETA * (t[m] - 1.0))
-        rho[m] += g
-        grad[m] += (-2.0 * _BETA * inv_r2[a] * g)[:, None] * d[m]
+        R = radii[a]
+        rc = R * np.sqrt(_CUT2)
+        i0 = np.maximum(np.floor((centers[a] - rc - lo) / h).astype(int), 0)
+        i1 = np.minimum(np.ceil((centers[a] + rc - lo) / h).astype(int) + 1, np.array(shape))
+        xs = [lo[d] + h * np.arange(i0[d], i1[d]) - centers[a, d] for d in range(3)]
+        t = (xs[0][:, None, None] ** 2 + xs[1][None, :, None] ** 2 + xs[2][None, None, :] ** 2) / (R * R)
+        rho[i0[0]:i1[0], i0[1]:i1[1], i0[2]:i1[2]] += np.exp(-_BETA * (np.minimum(t, _CUT2) - 1.0))
+    return rho - 1.0
+
+
+def _density_points(P, centers, radii):
+    """rho(P) and grad rho(P) using a cell list over the atoms (cutoff 4 R)."""
+    from scipy.spatial import cKDTree
+
+    rmax = float(radii.max()) * np.sqrt(_CUT2)
+    tree = cKDTree(centers)
+    lists = tree.query_ball_point(P, rmax)
+    cnt = np.fromiter((len(l) for l in lists), dtype=np.int64, count=len(lists))
+    ip = np.repeat(np.arange(P.shape[0]), cnt)
+    ia = np.fromiter((j for l in lists for j in l), dtype=np.int64, count=int(cnt.sum()))
+    d = P[ip] - centers[ia]
+    inv_r2 = 1.0 / radii[ia] ** 2
+    t = np.einsum("ij,ij->i", d, d) * inv_r2
+    g = np.exp(-_BETA * (np.minimum(t, _CUT2) - 1.0)) * (t < _CUT2)
+    rho = np.bincount(ip, weights=g, minlength=P.shape[0])
+    coef = -2.0 * _BETA * inv_r2 * g
+    grad = np.stack([np.bincount(ip, weights=coef * d[:, k], minlength=P.shape[0]) for k in range(3)], 1)
     return rho, grad
+
+
+def _density(points: np.ndarray, centers: np.ndarray, radii: np.ndarray):
+    return _density_points(points, centers, radii)
 
 
 # The six tetrahedra of a cube that share the main diagonal 0-6 (cube corners
@@ -349,16 +389,75 @@ def _is_closed_manifold(f: np.ndarray) -> bool:
     return bool(np.all(np.isin(rev, directed)))
 
 
-def synthetic_molecule(n_atoms: int, seed: int, ball_radius: float | None = None,
-                       grid_h: float = 0.5, pad: float = 3.0, centers=None, radii=None):
-    """Seeded globular molecule and its Gaussian-density surface.
+def _face_normals(V, F):
+    cr = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    return cr / np.maximum(np.linalg.norm(cr, axis=1, keepdims=True), 1e-300)
 
-    Atoms: sequential random packing in a ball (radius defaults to
-    20 A * (n_atoms/1000)**(1/3)), radii U[1.2, 2.0] A; charges N(0, 0.4) e
-    shifted so the net charge is an integer. Surface: {rho = 1} with
-    rho = sum_a exp(-2 (|x-c_a|^2/R_a^2 - 1)), extracted by marching
-    tetrahedra on a grid of spacing grid_h; largest component kept; vertex
-    normals -grad rho/|grad rho| (analytic).
+
+def _project(V, centers, radii, max_step):
+    """Two Newton steps onto rho = 1 along grad rho, each step length-limited."""
+    for _ in range(2):
+        rho, g = _density_points(V, centers, radii)
+        g2 = np.einsum("ij,ij->i", g, g)
+        ok = g2 > 1e-20
+        step = np.zeros_like(V)
+        step[ok] = ((rho[ok] - 1.0) / g2[ok])[:, None] * g[ok]
+        ln = np.linalg.norm(step, axis=1, keepdims=True)
+        step *= np.minimum(1.0, max_step / np.maximum(ln, 1e-300))
+        V = V - step
+    return V
+
+
+def _smooth_on_surface(V, F, centers, radii, iters=6, step=0.5):
+    """Tangential Laplacian smoothing (step-limited) with projection back onto rho = 1."""
+    nv = V.shape[0]
+    e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]], 0)
+    deg = np.bincount(e[:, 0], minlength=nv).astype(np.float64)
+    h = float(np.median(np.linalg.norm(V[e[:, 0]] - V[e[:, 1]], axis=1)))
+    for _ in range(iters):
+        nb = np.stack([np.bincount(e[:, 0], weights=V[e[:, 1], k], minlength=nv) for k in range(3)], 1)
+        lap = nb / deg[:, None] - V
+        _, g = _density_points(V, centers, radii)
+        n = g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-300)
+        lap -= np.einsum("ij,ij->i", lap, n)[:, None] * n
+        ln = np.linalg.norm(lap, axis=1, keepdims=True)
+        lap *= np.minimum(1.0, 0.3 * h / np.maximum(ln, 1e-300))
+        V = _project(V + step * lap, centers, radii, 0.3 * h)
+    return V
+
+
+def _surface(centers, radii, grid_h, pad=3.0, smooth_iters=6):
+    R = radii + _PROBE
+    lo = (centers - R[:, None]).min(axis=0) - pad
+    hi = (centers + R[:, None]).max(axis=0) + pad
+    lo = lo - 0.3183098861837907 * grid_h  # irrational offset: no grid point sits on the isosurface
+    shape = tuple((np.ceil((hi - lo) / grid_h).astype(int) + 1).tolist())
+    field = _density_grid(centers, R, lo, shape, grid_h)
+    # keep grid values away from the isovalue so no surface vertex lands within 5% of a cell
+    # corner (prevents sliver triangles); the crossing moves by at most that much
+    eps = 0.05 * np.median(np.abs(np.diff(field, axis=0))) + 1e-12
+    small = np.abs(field) < eps
+    field[small] = np.where(field[small] >= 0.0, eps, -eps)
+    v, f = _marching_tets(field, lo, grid_h)
+    v, f = _clean_mesh(v, f)
+    if smooth_iters:
+        v = _smooth_on_surface(v, f, centers, R, iters=smooth_iters)
+    _, grad = _density_points(v, centers, R)
+    n = -grad / np.linalg.norm(grad, axis=1, keepdims=True)
+    return v, f, n
+
+
+def synthetic_molecule(n_atoms: int, seed: int, ball_radius: float | None = None, n_faces: int | None = None,
+                       grid_h: float | None = None, centers=None, radii=None):
+    """Seeded globular molecule and its Gaussian-density surface (stand-in for the paper's
+    MSMS surfaces of protein 1ajj, Sec. 3.3).
+
+    Atoms: sequential random packing in a ball (radius 20 A * (n_atoms/1000)**(1/3) by
+    default), radii U[1.2, 2.0] A; charges N(0, 0.4) e shifted so the net charge is an integer.
+    Surface: {rho = 1}, rho = sum_a exp(-(|x - c_a|^2/(R_a + 0.6)^2 - 1)), by marching
+    tetrahedra; the largest component is kept, vertices are smoothed tangentially (6 passes) and
+    projected back onto the isosurface, normals are -grad rho/|grad rho| (analytic). The grid spacing is
+    grid_h, or chosen to give about n_faces triangles (default 40 per atom).
 
     Returns (V, F, N, charges[n,4]).
     """
@@ -368,21 +467,16 @@ def synthetic_molecule(n_atoms: int, seed: int, ball_radius: float | None = None
             ball_radius = 20.0 * (n_atoms / 1000.0) ** (1.0 / 3.0)
         centers, radii = _place_atoms(n_atoms, ball_radius, rng)
     charges = _charges_for(centers, rng)
-    lo = (centers - radii[:, None]).min(axis=0) - pad
-    hi = (centers + radii[:, None]).max(axis=0) + pad
-    # offset the grid by an irrational fraction to avoid field values of exactly 0
-    lo = lo - 0.3183098861837907 * grid_h
-    shape = np.ceil((hi - lo) / grid_h).astype(int) + 1
-    gx = lo[0] + grid_h * np.arange(shape[0])
-    gy = lo[1] + grid_h * np.arange(shape[1])
-    gz = lo[2] + grid_h * np.arange(shape[2])
-    P = np.stack(np.meshgrid(gx, gy, gz, indexing="ij"), -1).reshape(-1, 3)
-    rho, _ = _density(P, centers, radii)
-    field = (rho - 1.0).reshape(tuple(shape))
-    v, f = _marching_tets(field, lo, grid_h)
-    v, f = _clean_mesh(v, f)
-    _, grad = _density(v, centers, radii)
-    n = -grad / np.linalg.norm(grad, axis=1, keepdims=True)
+    if grid_h is None:
+        # smoothing leaves the triangle count unchanged: search the spacing on raw extractions
+        target = n_faces if n_faces is not None else 40 * centers.shape[0]
+        grid_h = 1.0
+        for _ in range(2):
+            _, f, _ = _surface(centers, radii, grid_h, smooth_iters=0)
+            if abs(f.shape[0] / target - 1.0) < 0.1:
+                break
+            grid_h = grid_h * np.sqrt(f.shape[0] / target)
+    v, f, n = _surface(centers, radii, grid_h)
     return (
         np.ascontiguousarray(v, dtype=np.float64),
         np.ascontiguousarray(f, dtype=np.int32),
@@ -391,7 +485,7 @@ def synthetic_molecule(n_atoms: int, seed: int, ball_radius: float | None = None
     )
 
 
-def two_globule_complex(n_atoms_each: int, seed_a: int, seed_b: int, grid_h: float = 0.5):
+def two_globule_complex(n_atoms_each: int, seed_a: int, seed_b: int, n_faces: int | None = None):
     """Two seeded globules in contact (centres 2*R_g - 2 A apart), one surface."""
     rg = 20.0 * (n_atoms_each / 1000.0) ** (1.0 / 3.0)
     ca, ra = _place_atoms(n_atoms_each, rg, np.random.default_rng(seed_a))
@@ -400,7 +494,7 @@ def two_globule_complex(n_atoms_each: int, seed_a: int, seed_b: int, grid_h: flo
     centers = np.concatenate([ca, cb], 0)
     radii = np.concatenate([ra, rb], 0)
     return synthetic_molecule(2 * n_atoms_each, seed_a * 1000 + seed_b, centers=centers,
-                              radii=radii, grid_h=grid_h)
+                              radii=radii, n_faces=n_faces)
 
 
 def mesh_stats(V: np.ndarray, F: np.ndarray) -> dict:

@@ -22,3 +22,30 @@ def test_ball_charges_seeded():
     assert np.array_equal(q1, q2)
     assert np.all(np.linalg.norm(q1[:, :3], axis=1) <= 8.0)
     assert np.all(np.abs(q1[:, 3]) <= 1.0)
+
+
+def _quality(V, F, N):
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    cr = np.cross(b - a, c - a)
+    fn = cr / np.linalg.norm(cr, axis=1, keepdims=True)
+    agree = np.einsum("ij,ij->i", fn, (N[F[:, 0]] + N[F[:, 1]] + N[F[:, 2]]) / 3)
+    return agree
+
+
+def test_synthetic_molecule_surface():
+    """Gaussian-density molecule: closed, consistently oriented, outward, genus 0 here, normals
+    unit and agreeing with the faces, integer net charge, seeded and reproducible, charges inside."""
+    V, F, N, Q = synth.synthetic_molecule(60, 7)
+    st = synth.mesh_stats(V, F)
+    assert st["closed_oriented"] and st["euler"] == 2
+    assert abs(F.shape[0] - 40 * 60) < 0.15 * 40 * 60
+    assert np.allclose(np.linalg.norm(N, axis=1), 1.0)
+    assert np.all(_quality(V, F, N) > 0.3)  # no face tilted more than ~72 deg from its normals
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    assert np.einsum("ij,ij->i", a, np.cross(b, c)).sum() > 0  # positive enclosed volume
+    assert abs(Q[:, 3].sum() - round(Q[:, 3].sum())) < 1e-12
+    V2, F2, N2, Q2 = synth.synthetic_molecule(60, 7)
+    assert np.array_equal(V, V2) and np.array_equal(F, F2) and np.array_equal(Q, Q2)
+    # every charge (atom centre) is inside: nearest surface vertex is farther than 0.5 A
+    d = np.min(np.linalg.norm(V[None, :, :] - Q[:, None, :3], axis=2), axis=1)
+    assert np.all(d > 0.5)
