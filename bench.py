@@ -52,7 +52,7 @@ WORKLOAD = {
 OPS_PER_PAIR = 36  # FP32 FMA-pipe instructions per pair in the both-rows far-field kernel
 MUFU_PER_PAIR = 2  # rsqrt.approx + ex2.approx
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "farfield32_c2_ico6_traffic.txt")
-FARFIELD_SRC = os.path.join(ROOT, "paper_1301_5914_gb300", "csrc", "k_farfield.cu")
+FARFIELD_SRC = [os.path.join(ROOT, "paper_1301_5914_gb300", "csrc", f) for f in ("k_farfield.cu", "ff_body.cuh")]
 
 
 def _inputs():
@@ -133,7 +133,7 @@ def _traffic_per_launch():
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
-        h = hashlib.sha256(open(FARFIELD_SRC, "rb").read()).hexdigest()
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in FARFIELD_SRC)).hexdigest()
         if rec.get("kernel_source_sha256") == h:
             return int(rec["dram_bytes_per_launch_full_size"])
     except (OSError, ValueError, KeyError):

@@ -185,6 +185,52 @@ int hobi_kernel_launches(hobi_t h, int64_t* n);
 /* Free every resource of the handle (NULL is a no-op). */
 void hobi_destroy(hobi_t h);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched solve: many molecules (same eps1, eps2, kappa) solved together. Every GMRES step
+ * runs one persistent far-field launch over a task list covering every unconverged molecule,
+ * and the Arnoldi/Givens work of all molecules in one set of launches (replayed as a CUDA
+ * graph); converged molecules drop out. Each molecule follows exactly the single-molecule
+ * method above (Sec. 2.2-2.3, Eqs. eqdbef3-eqdbef6), with its own Krylov space, residual
+ * test and restart.
+ * ------------------------------------------------------------------------------------- */
+typedef struct hobi_batch_ctx* hobi_batch_t;
+
+/* Molecule m owns rows [vertex_offsets[m], vertex_offsets[m+1]) of vertices/vertex_normals,
+ * [face_offsets[m], face_offsets[m+1]) of faces (0-based indices LOCAL to molecule m's
+ * vertices) and [charge_offsets[m], charge_offsets[m+1]) of charges. The three offset arrays
+ * (n_mol + 1 int64 each, starting at 0) are HOST arrays; the data arrays follow opt.mem_device.
+ * Per-molecule errors are reported as for hobi_setup, prefixed with the molecule index. */
+int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* vertex_offsets,
+                     const int32_t* faces, const int64_t* face_offsets, const double* vertex_normals,
+                     const double* charges, const int64_t* charge_offsets, double eps1, double eps2,
+                     double kappa, const hobi_options* opt, hobi_batch_t* out);
+
+/* n_mol, total vertices (sum of n_v) and total quadrature nodes (any pointer may be NULL). */
+int hobi_batch_sizes(hobi_batch_t b, int32_t* n_mol, int64_t* total_vertices, int64_t* total_nodes);
+
+int hobi_batch_set_precision(hobi_batch_t b, int32_t precision);
+
+/* Au = A u for every molecule; u and Au are the concatenation of the molecules' 2 n_v blocks
+ * ([phi_m; dphi_m] in molecule order). */
+int hobi_matvec_batch(hobi_batch_t b, const double* u, double* Au);
+
+/* GMRES for every molecule (tol, max_it and the restart length apply per molecule).
+ * phi, dphi: sum n_v doubles each, molecule blocks at vertex_offsets (either may be NULL).
+ * iterations, status: n_mol entries each (HOST, may be NULL): Krylov iterations and
+ * HOBI_OK / HOBI_ERR_NOT_CONVERGED / HOBI_ERR_BREAKDOWN per molecule. info (nullable)
+ * aggregates: batched steps, all converged, worst residual, solve time, pair evaluations.
+ * Returns HOBI_OK when every molecule converged. */
+int hobi_solve_batch(hobi_batch_t b, double tol, int32_t max_it, double* phi, double* dphi,
+                     int32_t* iterations, int32_t* status, hobi_solve_info* info);
+
+/* Solvation energy of every molecule (Eq. solvation_energy), e_sol[n_mol] HOST, kcal/mol. */
+int hobi_energy_batch(hobi_batch_t b, double* e_sol);
+
+/* CUDA kernels launched by the batch handle and its per-molecule tables since setup. */
+int hobi_batch_kernel_launches(hobi_batch_t b, int64_t* n);
+
+void hobi_destroy_batch(hobi_batch_t b);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* hobi_last_error(void);
 

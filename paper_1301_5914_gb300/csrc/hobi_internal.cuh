@@ -129,4 +129,66 @@ cudaError_t launch_finish_cycle(const double* H, int m, const double* g, const G
                                 const double* Vb, int64_t ld, double* x, int64_t n, cudaStream_t s);
 cudaError_t launch_residual_start(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t s);
 
+
+// ---- batched solve (k_batch.cu) ----
+struct MolDesc {          // one molecule's device tables (owned by its single-molecule handle)
+  const int* F;
+  const double *ny, *nnu, *nW, *center;
+  const int *inc_ptr, *inc_face;
+  const double* corr;
+  const float4* tgt32;
+  const double* tgt64;
+  float4* src32;
+  double* src64;
+  double* part;           // [chunks][2 nv] partials of the batched far field
+  int nv, n_nodes, chunks;
+  double eps;
+  int64_t u_off;          // offset of the molecule's 2 nv block in the concatenated vectors
+};
+struct FFTask {           // one persistent far-field work item
+  int mol, bx, t0, t1, chunk;
+};
+struct Segment {          // piece of the concatenated vector inside one molecule
+  int64_t start;
+  int len, mol;
+};
+struct BatchState {
+  int k;                  // column being built in the current cycle (shared by all molecules)
+  int it;                 // batched iterations run
+};
+struct MolState {
+  int converged, breakdown;
+  int cols;               // columns this molecule built in the current cycle
+  int it;                 // this molecule's Krylov iterations
+  double bnorm, rel, tol, hn;
+};
+constexpr int kSegLen = 4096;
+constexpr int kTilesPerTask = 16;
+cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const int64_t* node_off, int64_t total_nodes,
+                                const double* u, const int* kptr, int64_t ld, const MolState* ms, cudaStream_t s);
+cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,
+                                  const MolState* ms, double eps, double kappa, int grid, cudaStream_t s);
+int farfield_batch_blocks_per_sm(bool fp32);
+cudaError_t launch_combine_batch(const MolDesc* mols, int nmol, const int64_t* vert_off, int64_t total_verts,
+                                 const double* u, const int* kptr, int64_t ld, double* Au, const MolState* ms,
+                                 cudaStream_t s);
+cudaError_t launch_bdots(const double* Vb, int64_t ld, const double* w, const Segment* seg, int nseg,
+                         const BatchState* gs, const MolState* ms, int self, double* part, cudaStream_t s);
+cudaError_t launch_breduce(const double* part, int nseg, const int* mol_seg, int nmol, int m, const BatchState* gs,
+                           const MolState* ms, int self, int ldc, double* c, double* hcol, int accumulate,
+                           cudaStream_t s);
+cudaError_t launch_baxpy(const double* Vb, int64_t ld, const double* c, int ldc, const Segment* seg, int nseg,
+                         const BatchState* gs, const MolState* ms, double* w, cudaStream_t s);
+cudaError_t launch_bgivens(BatchState* gs, MolState* ms, int nmol, int m, double* H, double* cs, double* sn, double* g,
+                           const double* hcol, const double* nrm, int ldc, cudaStream_t s);
+cudaError_t launch_bnext(double* Vb, int64_t ld, const double* w, const Segment* seg, int nseg, const BatchState* gs,
+                         const MolState* ms, cudaStream_t s);
+cudaError_t launch_badvance(BatchState* gs, cudaStream_t s);
+cudaError_t launch_bcycle_start(double* Vb, const Segment* seg, int nseg, BatchState* gs, MolState* ms, int nmol,
+                                const double* nrm, int ldc, double* g, int m, int first, cudaStream_t s);
+cudaError_t launch_bfinish(const double* H, int m, const double* g, const MolState* ms, int nmol, double* y,
+                           const double* Vb, int64_t ld, const Segment* seg, int nseg, double* x, cudaStream_t s);
+cudaError_t launch_bresidual(const double* b, const double* Ax, double* r, const Segment* seg, int nseg,
+                             const MolState* ms, cudaStream_t s);
+
 }  // namespace hobi

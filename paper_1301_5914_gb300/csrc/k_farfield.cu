@@ -23,29 +23,10 @@
 // written as FP64 per (source chunk, target); the combine kernel adds the chunks in a fixed order.
 #include <math.h>
 
-#include "hobi_internal.cuh"
+#include "ff_body.cuh"
 
 namespace hobi {
 namespace {
-
-__device__ __forceinline__ float rsqrt_approx(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float exp2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-// hi + lo += v, error-free transformation of the addition (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
-  float s = __fadd_rn(hi, v);
-  float bp = __fsub_rn(s, hi);
-  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
-  hi = s;
-  lo = __fadd_rn(lo, err);
-}
 
 // ------------------------------------------------------------------ gather (per matvec)
 __global__ void k_gather32(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
@@ -55,22 +36,7 @@ __global__ void k_gather32(int n_nodes, int nv, const int* __restrict__ F, const
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= n_nodes) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
-  int j = node >> 2;
-  int a = F[3 * j], b = F[3 * j + 1], c = F[3 * j + 2];
-  const double* W = nW + 3 * (size_t)node;
-  double sig = (W[0] * u[nv + a] + W[1] * u[nv + b] + W[2] * u[nv + c]) * kInv4Pi;
-  double mu = (W[0] * u[a] + W[1] * u[b] + W[2] * u[c]) * kInv4Pi;
-  const double* y = ny + 3 * (size_t)node;
-  const double* n = nnu + 3 * (size_t)node;
-  // {-y_x, -y_x, -y_y, -y_y}, {-y_z, -y_z, sigma, sigma}, {m_x, m_x, m_y, m_y}, {m_z, m_z, sigma/eps, sigma/eps}
-  const float yx = (float)(center[0] - y[0]), yy = (float)(center[1] - y[1]), yz = (float)(center[2] - y[2]);
-  const float sg = (float)sig, se = (float)(sig * inv_eps);
-  const float mx = (float)(mu * n[0]), my = (float)(mu * n[1]), mz = (float)(mu * n[2]);
-  float4* o = src + 4 * (size_t)node;
-  o[0] = make_float4(yx, yx, yy, yy);
-  o[1] = make_float4(yz, yz, sg, sg);
-  o[2] = make_float4(mx, mx, my, my);
-  o[3] = make_float4(mz, mz, se, se);
+  ff::gather32_node(node, nv, F, ny, nnu, nW, center, u, inv_eps, src);
 }
 
 __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
@@ -80,22 +46,7 @@ __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= n_nodes) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
-  int j = node >> 2;
-  int a = F[3 * j], b = F[3 * j + 1], c = F[3 * j + 2];
-  const double* W = nW + 3 * (size_t)node;
-  double sig = (W[0] * u[nv + a] + W[1] * u[nv + b] + W[2] * u[nv + c]) * kInv4Pi;
-  double mu = (W[0] * u[a] + W[1] * u[b] + W[2] * u[c]) * kInv4Pi;
-  const double* y = ny + 3 * (size_t)node;
-  const double* n = nnu + 3 * (size_t)node;
-  double* o = src + 8 * (size_t)node;
-  o[0] = y[0] - center[0];
-  o[1] = y[1] - center[1];
-  o[2] = y[2] - center[2];
-  o[3] = sig;
-  o[4] = mu * n[0];
-  o[5] = mu * n[1];
-  o[6] = mu * n[2];
-  o[7] = 0.0;
+  ff::gather64_node(node, nv, F, ny, nnu, nW, center, u, src);
 }
 
 // Padding nodes: far away with zero densities, so every term they add is exactly zero.
@@ -111,158 +62,25 @@ __global__ void k_pad(int n_nodes, int n_pad, float4* src32, double* src64) {
   o[3] = o[4] = o[5] = o[6] = o[7] = 0.0;
 }
 
-// ------------------------------------------------------------------ far field, FP32 bulk
-__device__ __forceinline__ float2 pair_of(float a) { return make_float2(a, a); }
-
+// ------------------------------------------------------------------ far field kernels
 template <bool ROW2>
 __global__ void __launch_bounds__(kFF32Threads, 2)
     k_farfield32(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src, int n_tiles, int tpc,
                  float neg_kl2e, float kap, float eps, double* __restrict__ part, int64_t ldp) {
-  constexpr int T = kFF32Targets, TP = kFF32Targets / 2, NT = kFF32Threads;
   __shared__ float4 sh[4 * kTile];
-  float2 px[TP], py[TP], pz[TP];  // target k = 2p + lane
-  float qx[T], qy[T], qz[T];
-  float h1[T], l1[T], h2[T], l2[T];
-  const int base = blockIdx.x * (NT * T) + threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < T; ++k) {
-    int i = min(base + k * NT, nt - 1);
-    float4 a = tgt[2 * (size_t)i], b = tgt[2 * (size_t)i + 1];
-    if (k & 1) {
-      px[k >> 1].y = a.x; py[k >> 1].y = a.y; pz[k >> 1].y = a.z;
-    } else {
-      px[k >> 1].x = a.x; py[k >> 1].x = a.y; pz[k >> 1].x = a.z;
-    }
-    qx[k] = b.x; qy[k] = b.y; qz[k] = b.z;
-    h1[k] = l1[k] = h2[k] = l2[k] = 0.f;
-  }
-  const float2 nk2 = pair_of(neg_kl2e), kap2 = pair_of(kap), eps2 = pair_of(eps);
-  const float2 m1 = pair_of(-1.f), three = pair_of(3.f), m3 = pair_of(-3.f);
   const int t0 = blockIdx.y * tpc;
-  const int t1 = min(n_tiles, t0 + tpc);
-  for (int tile = t0; tile < t1; ++tile) {
-    __syncthreads();
-    const float4* g = src + (size_t)tile * (4 * kTile);
-    for (int q = threadIdx.x; q < 4 * kTile; q += NT) sh[q] = g[q];
-    __syncthreads();
-    float2 a1[TP], wx[TP], wy[TP], wz[TP];
-#pragma unroll
-    for (int k = 0; k < TP; ++k) a1[k] = wx[k] = wy[k] = wz[k] = pair_of(0.f);
-#pragma unroll 2
-    for (int s = 0; s < kTile; ++s) {
-      const float4 A = sh[4 * s], B = sh[4 * s + 1], C = sh[4 * s + 2], D = sh[4 * s + 3];
-      const float2 nyx = make_float2(A.x, A.y), nyy = make_float2(A.z, A.w), nyz = make_float2(B.x, B.y);
-      const float2 sg = make_float2(B.z, B.w), mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w);
-      const float2 mz = make_float2(D.x, D.y), se = make_float2(D.z, D.w);
-#pragma unroll
-      for (int k = 0; k < TP; ++k) {
-        const float2 dx = __fadd2_rn(px[k], nyx), dy = __fadd2_rn(py[k], nyy), dz = __fadd2_rn(pz[k], nyz);
-        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-        const float2 r = __fmul2_rn(r2, ir);
-        const float2 ea = __fmul2_rn(nk2, r);
-        const float2 E = make_float2(exp2_approx(ea.x), exp2_approx(ea.y));
-        const float2 aym = __ffma2_rn(dz, mz, __ffma2_rn(dy, my, __fmul2_rn(dx, mx)));  // d . m
-        const float2 ir2 = __fmul2_rn(ir, ir);
-        const float2 ir3 = __fmul2_rn(ir2, ir);
-        const float2 u3 = __fmul2_rn(aym, ir3);                                       // (d . m)/r^3
-        const float2 kr = __fmul2_rn(kap2, r);
-        const float2 P = __ffma2_rn(E, kr, E);
-        // row 1: (1 - E)/r sigma + (eps P - 1)(d . m)/r^3
-        a1[k] = __ffma2_rn(__ffma2_rn(make_float2(-E.x, -E.y), ir, ir), sg, a1[k]);
-        a1[k] = __ffma2_rn(__ffma2_rn(eps2, P, m1), u3, a1[k]);
-        if (ROW2) {
-          const float2 Q3 = __ffma2_rn(E, __ffma2_rn(kr, __fadd2_rn(kr, three), three), m3);  // Q - 3
-          const float2 w = __ffma2_rn(P, ir3, make_float2(-ir3.x, -ir3.y));                  // (P - 1)/r^3
-          const float2 q2 = __fmul2_rn(Q3, ir2);
-          // (P/eps - 1) sigma / r^3 - (Q - 3)(d . m)/r^5
-          const float2 sv = __ffma2_rn(make_float2(-q2.x, -q2.y), u3,
-                                       __fmul2_rn(__ffma2_rn(P, se, make_float2(-sg.x, -sg.y)), ir3));
-          wx[k] = __ffma2_rn(w, mx, __ffma2_rn(sv, dx, wx[k]));
-          wy[k] = __ffma2_rn(w, my, __ffma2_rn(sv, dy, wy[k]));
-          wz[k] = __ffma2_rn(w, mz, __ffma2_rn(sv, dz, wz[k]));
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < TP; ++k) {
-      two_sum_acc(h1[2 * k], l1[2 * k], a1[k].x);
-      two_sum_acc(h1[2 * k + 1], l1[2 * k + 1], a1[k].y);
-      if (ROW2) {
-        two_sum_acc(h2[2 * k], l2[2 * k], fmaf(qx[2 * k], wx[k].x, fmaf(qy[2 * k], wy[k].x, qz[2 * k] * wz[k].x)));
-        two_sum_acc(h2[2 * k + 1], l2[2 * k + 1],
-                    fmaf(qx[2 * k + 1], wx[k].y, fmaf(qy[2 * k + 1], wy[k].y, qz[2 * k + 1] * wz[k].y)));
-      }
-    }
-  }
-  double* out = part + (size_t)blockIdx.y * ldp;
-#pragma unroll
-  for (int k = 0; k < T; ++k) {
-    int i = base + k * NT;
-    if (i < nt) {
-      out[i] = (double)h1[k] + (double)l1[k];
-      if (ROW2) out[nt + i] = (double)h2[k] + (double)l2[k];
-    }
-  }
+  ff::ff32_block<ROW2>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), neg_kl2e, kap, eps,
+                       part + (size_t)blockIdx.y * ldp, blockIdx.x, sh);
 }
 
-// ------------------------------------------------------------------ far field, plain FP64
 template <bool ROW2>
 __global__ void __launch_bounds__(kFF64Threads)
     k_farfield64(const double* __restrict__ tgt, int nt, const double* __restrict__ src, int n_tiles, int tpc,
                  double kap, double eps, double ieps, double* __restrict__ part, int64_t ldp) {
-  constexpr int T = kFF64Targets, NT = kFF64Threads;
   __shared__ double2 sh[4 * kTile];
-  double px[T], py[T], pz[T], qx[T], qy[T], qz[T], a1[T], a2[T];
-  const int base = blockIdx.x * (NT * T) + threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < T; ++k) {
-    int i = min(base + k * NT, nt - 1);
-    const double* t = tgt + 8 * (size_t)i;
-    px[k] = t[0]; py[k] = t[1]; pz[k] = t[2];
-    qx[k] = t[4]; qy[k] = t[5]; qz[k] = t[6];
-    a1[k] = a2[k] = 0.0;
-  }
   const int t0 = blockIdx.y * tpc;
-  const int t1 = min(n_tiles, t0 + tpc);
-  for (int tile = t0; tile < t1; ++tile) {
-    __syncthreads();
-    const double2* g = reinterpret_cast<const double2*>(src) + (size_t)tile * (4 * kTile);
-    for (int q = threadIdx.x; q < 4 * kTile; q += NT) sh[q] = g[q];
-    __syncthreads();
-    for (int s = 0; s < kTile; ++s) {
-      const double2 y01 = sh[4 * s], y2s = sh[4 * s + 1], m01 = sh[4 * s + 2], m2 = sh[4 * s + 3];
-#pragma unroll
-      for (int k = 0; k < T; ++k) {
-        double dx = px[k] - y01.x, dy = py[k] - y01.y, dz = pz[k] - y2s.x;
-        double r2 = dx * dx + dy * dy + dz * dz;
-        double r = sqrt(r2);
-        double ir = 1.0 / r;
-        double kr = kap * r;
-        double E = exp(-kr);
-        double P = E * (1.0 + kr);
-        double aym = dx * m01.x + dy * m01.y + dz * m2.x;
-        double ir3 = ir * ir * ir;
-        a1[k] += (1.0 - E) * ir * y2s.y + (eps * P - 1.0) * ir3 * aym;
-        if (ROW2) {
-          double Q3 = E * (3.0 + kr * (3.0 + kr)) - 3.0;
-          double ir5 = ir3 * ir * ir;
-          double w = (P - 1.0) * ir3;
-          double sv = (P * ieps - 1.0) * ir3 * y2s.y - Q3 * ir5 * aym;
-          a2[k] += qx[k] * (w * m01.x + sv * dx) + qy[k] * (w * m01.y + sv * dy) + qz[k] * (w * m2.x + sv * dz);
-        }
-      }
-    }
-  }
-  double* out = part + (size_t)blockIdx.y * ldp;
-#pragma unroll
-  for (int k = 0; k < T; ++k) {
-    int i = base + k * NT;
-    if (i < nt) {
-      out[i] = a1[k];
-      if (ROW2) out[nt + i] = a2[k];
-    }
-  }
+  ff::ff64_block<ROW2>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), kap, eps, ieps, part + (size_t)blockIdx.y * ldp,
+                       blockIdx.x, sh);
 }
 
 // ------------------------------------------------------------------ combine
@@ -275,24 +93,7 @@ __global__ void k_combine(int nv, int chunks, const double* __restrict__ part, c
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
-  double s1 = 0.0, s2 = 0.0;
-  const size_t ldp = 2 * (size_t)nv;
-  for (int c = 0; c < chunks; ++c) {
-    s1 += part[c * ldp + i];
-    s2 += part[c * ldp + nv + i];
-  }
-  for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
-    const int* f = F + 3 * inc[e];
-    const double* C = corr + 12 * (size_t)e;
-#pragma unroll
-    for (int n = 0; n < 3; ++n) {
-      double dphi = u[nv + f[n]], phi = u[f[n]];
-      s1 += C[4 * n] * dphi + C[4 * n + 1] * phi;
-      s2 += C[4 * n + 2] * dphi + C[4 * n + 3] * phi;
-    }
-  }
-  Au[i] = 0.5 * (1.0 + eps) * u[i] - s1;
-  Au[nv + i] = 0.5 * (1.0 + 1.0 / eps) * u[nv + i] - s2;
+  ff::combine_vertex(i, nv, chunks, part, F, ptr, inc, corr, eps, u, Au);
 }
 
 __global__ void k_reduce_points(int np, int chunks, const double* __restrict__ part, double* __restrict__ phi) {

@@ -35,7 +35,8 @@ EXPORTS = [
     "hobi_solve", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
     "hobi_reaction_potential_noalloc", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches",
-    "hobi_destroy", "hobi_last_error",
+    "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
+    "hobi_matvec_batch", "hobi_solve_batch", "hobi_energy_batch", "hobi_batch_kernel_launches", "hobi_destroy_batch",
 ]
 
 
@@ -90,10 +91,20 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_kernel_launches.argtypes = [vp, C.POINTER(i64)]
     lib.hobi_destroy.argtypes = [vp]
     lib.hobi_destroy.restype = None
+    lib.hobi_setup_batch.argtypes = [C.c_int32, dp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                     C.POINTER(Options), C.POINTER(C.c_void_p)]
+    lib.hobi_batch_sizes.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(i64), C.POINTER(i64)]
+    lib.hobi_batch_set_precision.argtypes = [vp, C.c_int32]
+    lib.hobi_matvec_batch.argtypes = [vp, dp, dp]
+    lib.hobi_solve_batch.argtypes = [vp, C.c_double, C.c_int32, dp, dp, dp, dp, C.POINTER(SolveInfo)]
+    lib.hobi_energy_batch.argtypes = [vp, dp]
+    lib.hobi_batch_kernel_launches.argtypes = [vp, C.POINTER(i64)]
+    lib.hobi_destroy_batch.argtypes = [vp]
+    lib.hobi_destroy_batch.restype = None
     lib.hobi_last_error.argtypes = []
     lib.hobi_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("hobi_default_options", "hobi_destroy", "hobi_last_error"):
+        if name not in ("hobi_default_options", "hobi_destroy", "hobi_last_error", "hobi_destroy_batch"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -287,3 +298,119 @@ class Solver:
         n = C.c_int64()
         _check(self._lib.hobi_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(pairs)))
         return {"farfield_ms": ms.value, "launches": n.value, "pairs": pairs.value}
+
+
+class BatchSolver:
+    """Many molecules with the same eps1, eps2, kappa, solved together (wraps hobi_batch_t).
+
+    molecules: list of (V, F, N, charges) numpy arrays (host mode). With device=True the
+    concatenated inputs are first placed in CUDA torch tensors (device-pointer mode).
+    """
+
+    def __init__(self, molecules, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
+                 restart: int = 50, use_graph: bool = True, device_mode: bool = False, stream=None):
+        lib = load_library()
+        self._lib = lib
+        V = np.ascontiguousarray(np.concatenate([m[0] for m in molecules]), dtype=np.float64)
+        F = np.ascontiguousarray(np.concatenate([m[1] for m in molecules]), dtype=np.int32)
+        N = np.ascontiguousarray(np.concatenate([m[2] for m in molecules]), dtype=np.float64)
+        Q = np.ascontiguousarray(np.concatenate([np.asarray(m[3]).reshape(-1, 4) for m in molecules]),
+                                 dtype=np.float64)
+        self.vert_off = np.concatenate([[0], np.cumsum([m[0].shape[0] for m in molecules])]).astype(np.int64)
+        self.face_off = np.concatenate([[0], np.cumsum([m[1].shape[0] for m in molecules])]).astype(np.int64)
+        self.charge_off = np.concatenate([[0], np.cumsum([np.asarray(m[3]).reshape(-1, 4).shape[0]
+                                                          for m in molecules])]).astype(np.int64)
+        self.n_mol = len(molecules)
+        self.nv_total = int(self.vert_off[-1])
+        self.device_mode = device_mode
+        opt = Options()
+        lib.hobi_default_options(C.byref(opt))
+        opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
+        opt.restart = int(restart)
+        opt.use_graph = 1 if use_graph else 0
+        if device_mode:
+            import torch
+
+            dev = torch.device("cuda", torch.cuda.current_device())
+            opt.device = dev.index
+            opt.mem_device = 1
+            s = stream if stream is not None else torch.cuda.current_stream(dev)
+            opt.stream = C.c_void_p(s.cuda_stream)
+            self._keep = [torch.as_tensor(a, device=dev) for a in (V, F, N, Q)]
+            ptrs = [t.data_ptr() for t in self._keep]
+        else:
+            opt.device = -1
+            self._keep = [V, F, N, Q]
+            ptrs = [a.ctypes.data for a in self._keep]
+        h = C.c_void_p()
+        _check(lib.hobi_setup_batch(self.n_mol, ptrs[0], self.vert_off.ctypes.data, ptrs[1], self.face_off.ctypes.data,
+                                    ptrs[2], ptrs[3] if Q.size else None, self.charge_off.ctypes.data, float(eps1),
+                                    float(eps2), float(kappa), C.byref(opt), C.byref(h)))
+        self._h = h
+
+    def _out(self, n):
+        if self.device_mode:
+            import torch
+
+            return torch.empty(n, dtype=torch.float64, device=self._keep[0].device)
+        return np.empty(n, dtype=np.float64)
+
+    def _ptr(self, a):
+        return a.data_ptr() if self.device_mode else a.ctypes.data
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hobi_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: str):
+        _check(self._lib.hobi_batch_set_precision(self._h, HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64))
+
+    def split(self, a):
+        """Split a concatenated per-vertex array into per-molecule arrays."""
+        return [a[self.vert_off[i]:self.vert_off[i + 1]] for i in range(self.n_mol)]
+
+    def matvec(self, u):
+        """u: concatenation of the molecules' [phi; dphi] blocks (host mode: numpy)."""
+        n = 2 * self.nv_total
+        if self.device_mode:
+            import torch
+
+            u = torch.as_tensor(u, device=self._keep[0].device, dtype=torch.float64).contiguous()
+        else:
+            u = np.ascontiguousarray(u, dtype=np.float64)
+        out = self._out(n)
+        _check(self._lib.hobi_matvec_batch(self._h, self._ptr(u), self._ptr(out)))
+        return out
+
+    def solve(self, tol: float = 1e-6, max_it: int = 200, raise_on_fail: bool = True):
+        """Returns (phi per molecule, dphi per molecule, info); info has per-molecule iterations/status."""
+        phi = self._out(self.nv_total)
+        dphi = self._out(self.nv_total)
+        its = np.zeros(self.n_mol, dtype=np.int32)
+        st = np.zeros(self.n_mol, dtype=np.int32)
+        info = SolveInfo()
+        code = self._lib.hobi_solve_batch(self._h, float(tol), int(max_it), self._ptr(phi), self._ptr(dphi),
+                                          its.ctypes.data, st.ctypes.data, C.byref(info))
+        if raise_on_fail and code != HOBI_OK:
+            _check(code)
+        d = {"status": code, "steps": info.iterations, "converged": bool(info.converged),
+             "rel_residual": info.rel_residual, "solve_ms": info.solve_ms, "farfield_pairs": info.farfield_pairs,
+             "iterations": its, "mol_status": st}
+        return self.split(phi), self.split(dphi), d
+
+    def energy(self) -> np.ndarray:
+        e = np.zeros(self.n_mol, dtype=np.float64)
+        _check(self._lib.hobi_energy_batch(self._h, e.ctypes.data))
+        return e
+
+    def kernel_launches(self) -> int:
+        n = C.c_int64()
+        _check(self._lib.hobi_batch_kernel_launches(self._h, C.byref(n)))
+        return int(n.value)

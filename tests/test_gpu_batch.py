@@ -1,0 +1,107 @@
+"""Batched solve (one persistent far-field launch per GMRES step for all molecules) against the
+single-molecule path and the oracle: every molecule's result must equal its own solve."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1301_5914_gb300 import hobi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+EPS1, EPS2, KAPPA = 2.0, 80.0, 0.1257
+
+
+@pytest.fixture(scope="module")
+def molecules():
+    """Uneven sizes: three icospheres (42, 642, 2562 vertices) and two small synthetic molecules."""
+    mols = []
+    for lvl, R, seed in ((1, 1.5, 11), (3, 4.0, 12), (4, 8.0, 13)):
+        V, F, N = synth.icosphere(lvl, R)
+        mols.append((V, F, N, synth.ball_charges(5, 0.6 * R, seed)))
+    for n_atoms, seed in ((40, 1001), (90, 1002)):
+        mols.append(synth.synthetic_molecule(n_atoms, seed))
+    return mols
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-8)])
+def test_batch_matches_single_solves(molecules, prec, tol):
+    """FP64: same arithmetic up to the order of FP64 chunk sums. FP32: the batch groups the
+    compensated tile sums in 16-tile tasks, the single plan in its own chunks -- a change far
+    below the FP32-bulk tolerance (1e-4)."""
+    bs = hobi.BatchSolver(molecules, EPS1, EPS2, KAPPA, precision=prec)
+    phis, dphis, info = bs.solve(1e-6, 200)
+    assert info["converged"] and np.all(info["mol_status"] == 0)
+    E = bs.energy()
+    for i, (V, F, N, Q) in enumerate(molecules):
+        s = hobi.Solver(V, F, N, Q, EPS1, EPS2, KAPPA, precision=prec)
+        p, d, inf = s.solve(1e-6, 200)
+        assert info["iterations"][i] == inf["iterations"]
+        assert _rel(phis[i], p) <= tol and _rel(dphis[i], d) <= tol
+        assert abs(E[i] - s.energy()) <= tol * abs(E[i])
+        s.close()
+    assert info["steps"] == max(info["iterations"])
+    bs.close()
+
+
+def test_batch_fp64_against_oracle(molecules):
+    bs = hobi.BatchSolver(molecules[:4], EPS1, EPS2, KAPPA, precision="fp64")
+    phis, dphis, info = bs.solve(1e-6, 200)
+    E = bs.energy()
+    for i, (V, F, N, Q) in enumerate(molecules[:4]):
+        orc = oracle.Problem(V, F, N, Q, EPS1, EPS2, KAPPA)
+        u_ref, it_ref, conv, _ = orc.gmres(1e-6)
+        assert info["iterations"][i] == it_ref
+        assert _rel(np.concatenate([phis[i], dphis[i]]), u_ref) <= 1e-10
+        assert abs(E[i] - orc.energy(u_ref)) <= 1e-10 * abs(E[i])
+
+
+def test_batch_matvec_and_device_mode(molecules):
+    import torch
+
+    bh = hobi.BatchSolver(molecules, EPS1, EPS2, KAPPA, precision="fp64")
+    bd = hobi.BatchSolver(molecules, EPS1, EPS2, KAPPA, precision="fp64", device_mode=True)
+    u = np.random.default_rng(0).normal(size=2 * bh.nv_total)
+    Au = bh.matvec(u)
+    assert np.array_equal(Au, bd.matvec(torch.as_tensor(u, device="cuda")).cpu().numpy())
+    # block m of A u is molecule m's own operator on its block
+    off = 0
+    for (V, F, N, Q) in molecules:
+        n = 2 * V.shape[0]
+        s = hobi.Solver(V, F, N, Q, EPS1, EPS2, KAPPA, precision="fp64")
+        assert np.max(np.abs(Au[off:off + n] - s.matvec(u[off:off + n]))) <= 1e-12 * np.max(np.abs(Au[off:off + n]))
+        off += n
+
+
+def test_batch_restart_and_not_converged(molecules):
+    bs = hobi.BatchSolver(molecules[:3], EPS1, EPS2, KAPPA, precision="fp64", restart=3)
+    phis, dphis, info = bs.solve(1e-8, 300)
+    assert info["converged"]
+    for i, (V, F, N, Q) in enumerate(molecules[:3]):
+        s = hobi.Solver(V, F, N, Q, EPS1, EPS2, KAPPA, precision="fp64", restart=3)
+        p, d, inf = s.solve(1e-8, 300)
+        assert info["iterations"][i] == inf["iterations"]
+        assert _rel(phis[i], p) <= 1e-10
+    phis, dphis, info = bs.solve(1e-14, 4, raise_on_fail=False)
+    assert info["status"] == hobi.HOBI_ERR_NOT_CONVERGED
+    assert np.all(info["mol_status"] == hobi.HOBI_ERR_NOT_CONVERGED)
+
+
+def test_batch_reports_bad_member():
+    V, F, N = synth.icosphere(2, 2.0)
+    Q = synth.point_charge(0, 0, 0, 1.0)
+    with pytest.raises(hobi.HobiError) as ei:
+        hobi.BatchSolver([(V, F, N, Q), (V, F[:-1], N, Q)], 1.0, 80.0, 0.0)
+    assert ei.value.code == hobi.HOBI_ERR_MESH and "molecule 1" in str(ei.value)
