@@ -14,6 +14,11 @@ value = far-field pair evaluations per second over the whole step (all ranks).
 With --gpus N > 1 (torchrun) every rank solves its own replica (no collective on
 the data path): weak scaling.
 
+--workload selects other configurations for explicit runs (the default is the
+one above): c3 (1000-atom synthetic molecule, ~40k triangles, eps1 = 2), c5 (two
+3000-atom globules in contact, ~120k triangles) and c4 (64 synthetic molecules of
+50-2000 atoms, log-uniform, solved as one batch).
+
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (matvec rows), same metric and unit.
 """
@@ -35,7 +40,7 @@ if ROOT not in sys.path:
 
 METRIC = "matvec pair-evals/s & %FP32 peak; GMRES time to 1e-6 (FP32-bulk vs FP64 plain)"
 UNIT = "pair-evals/s"
-WORKLOAD = {
+WORKLOAD_C2 = {
     "workload": "kirkwood_sphere_r10_ico6_10charges",
     "mesh": "icosphere level 6, radius 10 A, exact radial normals",
     "n_faces": 81920,
@@ -49,6 +54,10 @@ WORKLOAD = {
     "gmres_tol": 1e-6,
     "precision": "fp32-bulk far field (FP32 pair sums, compensated tile sums, FP64 GMRES/correction/energy)",
 }
+WORKLOAD = WORKLOAD_C2
+MOLECULE = {"eps1": 2.0, "eps2": 80.0, "kappa": 0.1257, "gmres_tol": 1e-6,
+            "precision": WORKLOAD_C2["precision"],
+            "surface": "Gaussian-density isosurface (marching tetrahedra, smoothed), density-gradient normals"}
 OPS_PER_PAIR = 36  # FP32 FMA-pipe instructions per pair in the both-rows far-field kernel
 MUFU_PER_PAIR = 2  # rsqrt.approx + ex2.approx
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "farfield32_c2_ico6_traffic.txt")
@@ -61,6 +70,46 @@ def _inputs():
     V, F, N = synth.icosphere(6, 10.0)
     Q = synth.ball_charges(10, 8.0, 2)
     return V, F, N, Q
+
+
+def _c4_member(m):
+    import numpy as np
+
+    from paper_1301_5914_gb300 import synth
+
+    n_atoms = int(round(np.exp(np.random.default_rng(1000 + m).uniform(np.log(50), np.log(2000)))))
+    return synth.synthetic_molecule(n_atoms, 1000 + m)
+
+
+def make_workload(name):
+    """(config dict, list of (V, F, N, Q) molecules); one molecule unless batched."""
+    from paper_1301_5914_gb300 import synth
+
+    if name == "c2l6":
+        return dict(WORKLOAD_C2), [_inputs()]
+    if name == "c3":
+        mol = synth.synthetic_molecule(1000, 3)
+        cfg = dict(MOLECULE, workload="synthetic_molecule_1000_atoms_seed3", n_atoms=1000)
+    elif name == "c5":
+        mol = synth.two_globule_complex(3000, 51, 52, n_faces=120000)
+        cfg = dict(MOLECULE, workload="two_globule_complex_2x3000_atoms_seeds51_52", n_atoms=6000)
+    elif name == "c4":
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            mols = pool.map(_c4_member, range(64))
+        cfg = dict(MOLECULE, workload="batch_64_synthetic_molecules_50_2000_atoms_seeds1000_1063",
+                   n_molecules=64, n_atoms=int(sum(m[3].shape[0] for m in mols)))
+        cfg.update(n_faces=int(sum(m[1].shape[0] for m in mols)), n_vertices=int(sum(m[0].shape[0] for m in mols)),
+                   n_nodes=int(sum(4 * m[1].shape[0] for m in mols)), n_charges=cfg["n_atoms"],
+                   faces_min_max=[int(min(m[1].shape[0] for m in mols)), int(max(m[1].shape[0] for m in mols))])
+        return cfg, mols
+    else:
+        raise ValueError(name)
+    V, F, N, Q = mol
+    cfg.update(n_faces=int(F.shape[0]), n_vertices=int(V.shape[0]), n_nodes=int(4 * F.shape[0]),
+               n_charges=int(Q.shape[0]))
+    return cfg, [mol]
 
 
 def _dist():
@@ -141,15 +190,17 @@ def _traffic_per_launch():
     return None
 
 
-def cpu_oracle_sample(V, F, N, Q, rows: int, seed: int = 0):
+def cpu_oracle_sample(V, F, N, Q, rows: int, params=None, seed: int = 0):
     """Time the FP64 oracle's matvec on `rows` sampled rows of the workload (bounded CPU work)."""
     import numpy as np
 
     import oracle
 
-    prob = oracle.Problem(V, F, N, Q, WORKLOAD["eps1"], WORKLOAD["eps2"], WORKLOAD["kappa"])
+    p = params or WORKLOAD
+    prob = oracle.Problem(V, F, N, Q, p["eps1"], p["eps2"], p["kappa"])
     rng = np.random.default_rng(seed)
     u = rng.normal(size=2 * prob.nv)
+    rows = min(rows, prob.nv)
     sel = np.sort(rng.choice(prob.nv, size=rows, replace=False))
     t0 = time.perf_counter()
     prob.matvec_rows(u, sel)
@@ -187,6 +238,7 @@ def run_reference(args):
 
 
 def run_ours(args):
+    cfg, mols = make_workload(args.workload)  # before any CUDA call (the c4 generator uses a spawn pool)
     import numpy as np
     import torch
 
@@ -199,20 +251,30 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    V, F, N, Q = _inputs()
-    e1, e2, ka, tol = WORKLOAD["eps1"], WORKLOAD["eps2"], WORKLOAD["kappa"], WORKLOAD["gmres_tol"]
-    Vd = torch.as_tensor(V, device=dev)
-    Fd = torch.as_tensor(F, dtype=torch.int32, device=dev)
-    Nd = torch.as_tensor(N, device=dev)
-    Qd = torch.as_tensor(Q, device=dev)
-    nv, nn, nc = V.shape[0], 4 * F.shape[0], Q.shape[0]
+    e1, e2, ka, tol = cfg["eps1"], cfg["eps2"], cfg["kappa"], cfg["gmres_tol"]
+    batched = len(mols) > 1
+    cat = lambda k, dt=np.float64: np.ascontiguousarray(np.concatenate([np.asarray(m[k]).reshape(-1, 4 if k == 3 else 3)
+                                                                         for m in mols]), dtype=dt)
+    Vh, Fh, Nh, Qh = cat(0), cat(1, np.int32), cat(2), cat(3)
+    Vd, Fd, Nd, Qd = (torch.as_tensor(a, device=dev) for a in (Vh, Fh, Nh, Qh))
     stream = torch.cuda.current_stream(dev)
+    energy_pairs = float(sum(m[3].shape[0] * 4.0 * m[1].shape[0] for m in mols))
 
-    def step(profile: bool):
-        s = hobi.Solver(Vd, Fd, Nd, Qd, e1, e2, ka, precision="fp32", stream=stream)
+    def make(precision, host=False):
+        if batched:
+            if host:
+                return hobi.BatchSolver(mols, e1, e2, ka, precision=precision)
+            return hobi.BatchSolver(mols, e1, e2, ka, precision=precision, device_arrays=(Vd, Fd, Nd, Qd), stream=stream)
+        if host:
+            pin = [torch.as_tensor(a).pin_memory() for a in (Vh, Fh, Nh, Qh)]
+            return hobi.Solver(*pin, e1, e2, ka, precision=precision)
+        return hobi.Solver(Vd, Fd, Nd, Qd, e1, e2, ka, precision=precision, stream=stream)
+
+    def step(profile: bool, precision="fp32", host=False):
+        s = make(precision, host)
         if profile:
             s.profile_enable(True)
-        phi, dphi, info = s.solve(tol, 200)
+        phi, dphi, info = s.solve(tol, 400)
         E = s.energy()
         prof = s.profile_read() if profile else None
         n_launch = s.kernel_launches()
@@ -233,16 +295,17 @@ def run_ours(args):
         flush.zero_()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        info, E, prof, nl, phi32, dphi32 = step(True)
+        info, E, prof, nl, _, _ = step(True)
         ev1.record(stream)
         torch.cuda.synchronize()
         times.append(ev0.elapsed_time(ev1))
         ff_ms += prof["farfield_ms"]
         ff_launch += prof["launches"]
         ff_pairs += prof["pairs"]
-        pairs_step.append(prof["pairs"])
+        # single: the profile includes the energy launch; batch: energies run per molecule
+        pairs_step.append(prof["pairs"] + (energy_pairs if batched else 0.0))
         launches += nl
-        iters.append(info["iterations"])
+        iters.append(info["iterations"].tolist() if batched else info["iterations"])
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -257,7 +320,6 @@ def run_ours(args):
     pairs_per_step = statistics.mean(pairs_step)
     value, ms_per_step = aggregate(per_rank, pairs_per_step, args.steps)
 
-    out = None
     if rank == 0:
         # roofline of the dominant kernel (far field, FP32 bulk, both rows), live CUDA-event timing
         props = torch.cuda.get_device_properties(dev)
@@ -272,11 +334,11 @@ def run_ours(args):
         avg_launch_s = ff_ms / ff_launch / 1e3
         pairs_per_launch = ff_pairs / ff_launch
         achieved = pairs_per_launch * OPS_PER_PAIR / avg_launch_s / 1e9
-        traffic = _traffic_per_launch()
+        traffic = _traffic_per_launch() if args.workload == "c2l6" else None
         fobs = clk.get("sm_mhz") or fmax
         roof = {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginst/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_farfield32<ROW2=true>",
+            "traffic": traffic, "kernel": "k_farfield_batch32" if batched else "k_farfield32<ROW2=true>",
             "algorithmic": f"{OPS_PER_PAIR} FP32 FMA-pipe instructions + {MUFU_PER_PAIR} MUFU per pair",
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src})",
             "pairs_per_s": pairs_per_launch / avg_launch_s,
@@ -289,61 +351,61 @@ def run_ours(args):
         gm = {"fp32_bulk_s": None, "fp64_plain_s": None}
         acc = {}
         if not args.no_fp64:
-            s64 = hobi.Solver(Vd, Fd, Nd, Qd, e1, e2, ka, precision="fp64", stream=stream)
-            p64, d64, i64 = s64.solve(tol, 200)
-            E64 = s64.energy()
-            s64.close()
-            s32 = hobi.Solver(Vd, Fd, Nd, Qd, e1, e2, ka, precision="fp32", stream=stream)
-            p32, d32, i32 = s32.solve(tol, 200)
-            E32 = s32.energy()
-            s32.close()
+            i64, E64, _, _, p64, d64 = step(False, "fp64")
+            i32, E32, _, _, p32, d32 = step(False, "fp32")
+            it32 = i32["iterations"].tolist() if batched else i32["iterations"]
+            it64 = i64["iterations"].tolist() if batched else i64["iterations"]
             gm = {"fp32_bulk_s": i32["solve_ms"] / 1e3, "fp64_plain_s": i64["solve_ms"] / 1e3,
-                  "iterations_fp32": i32["iterations"], "iterations_fp64": i64["iterations"],
-                  "speedup": i64["solve_ms"] / i32["solve_ms"]}
+                  "iterations_fp32": it32, "iterations_fp64": it64, "speedup": i64["solve_ms"] / i32["solve_ms"]}
+            if batched:
+                p32, p64 = torch.cat(list(map(torch.as_tensor, p32))), torch.cat(list(map(torch.as_tensor, p64)))
+                d32, d64 = torch.cat(list(map(torch.as_tensor, d32))), torch.cat(list(map(torch.as_tensor, d64)))
+                E32, E64 = np.asarray(E32), np.asarray(E64)
             rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-            acc = {"phi_rel_l2_fp32_vs_fp64": rel(p32, p64), "dphi_rel_l2_fp32_vs_fp64": rel(d32, d64),
-                   "E_sol_fp32": E32, "E_sol_fp64": E64, "E_rel_fp32_vs_fp64": abs(E32 - E64) / abs(E64)}
-            try:
-                from oracle import kirkwood as kw
+            acc = {"phi_rel_l2_fp32_vs_fp64": rel(p32, p64), "dphi_rel_l2_fp32_vs_fp64": rel(d32, d64)}
+            if batched:
+                acc["E_rel_fp32_vs_fp64_max"] = float(np.max(np.abs(E32 - E64) / np.abs(E64)))
+            else:
+                acc.update(E_sol_fp32=E32, E_sol_fp64=E64, E_rel_fp32_vs_fp64=abs(E32 - E64) / abs(E64))
+                if args.workload == "c2l6":
+                    try:
+                        from oracle import kirkwood as kw
 
-                e_ex = kw.solvation_energy(Q, 10.0, e1, e2, ka)
-                acc["E_sol_kirkwood"] = e_ex
-                acc["E_rel_fp64_vs_kirkwood"] = abs(E64 - e_ex) / abs(e_ex)
-            except ImportError:
-                pass
-        # end to end through the public API with host buffers (pinned), copies inside the timed region
-        Vh = torch.as_tensor(V).pin_memory()
-        Fh = torch.as_tensor(F, dtype=torch.int32).pin_memory()
-        Nh = torch.as_tensor(N).pin_memory()
-        Qh = torch.as_tensor(Q).pin_memory()
+                        e_ex = kw.solvation_energy(Qh, 10.0, e1, e2, ka)
+                        acc["E_sol_kirkwood"] = e_ex
+                        acc["E_rel_fp64_vs_kirkwood"] = abs(E64 - e_ex) / abs(e_ex)
+                    except ImportError:
+                        pass
+        # end to end through the public API with host buffers, copies inside the timed region
         e2e_t, e2e_pairs = [], []
         for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s = hobi.Solver(Vh, Fh, Nh, Qh, e1, e2, ka, precision="fp32")
-            _, _, inf = s.solve(tol, 200)
-            s.energy()
-            s.close()
+            inf, _, prof, _, _, _ = step(True, "fp32", host=True)
             e2e_t.append(time.perf_counter() - t0)
-            e2e_pairs.append(inf["iterations"] * nv * nn + nc * nn)
-        h2d = V.nbytes + F.astype("int32").nbytes + N.nbytes + Q.nbytes
-        d2h = 2 * nv * 8 + 8
+            e2e_pairs.append(prof["pairs"] + (energy_pairs if batched else 0.0))
+        h2d = Vh.nbytes + Fh.nbytes + Nh.nbytes + Qh.nbytes
+        d2h = 2 * Vh.shape[0] * 8 + 8 * len(mols)
         e2e = {"value": sum(e2e_pairs) / sum(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(e2e_t) / len(e2e_t)}
         # CPU baseline: the oracle on a bounded sample of the same workload (rank 0, N = 1 only)
         cpu = None
         if ws == 1 and not args.no_cpu:
-            val, dt, pairs, cores = cpu_oracle_sample(V, F, N, Q, args.cpu_rows)
+            big = max(range(len(mols)), key=lambda i: mols[i][1].shape[0])
+            V, F, N, Q = mols[big]
+            val, dt, pairs, cores = cpu_oracle_sample(V, F, N, Q, args.cpu_rows, cfg)
             cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"{args.cpu_rows} of {nv} matvec rows x {nn} nodes ({pairs:.3g} pairs, {dt:.1f} s)"}
+                   "sample": f"{min(args.cpu_rows, V.shape[0])} of {V.shape[0]} matvec rows x {4 * F.shape[0]} "
+                             f"nodes ({pairs:.3g} pairs, {dt:.1f} s)" + (f", molecule {big}" if batched else "")}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(WORKLOAD, parallelism=f"replicas x{ws}" if ws > 1 else "single GPU",
+            "config": dict(cfg, parallelism=f"replicas x{ws}" if ws > 1 else "single GPU",
                            l2="flushed between timed steps (256 MB write)",
-                           pairs_per_step=pairs_per_step, gmres_iterations=iters[-1], E_sol=E),
+                           pairs_per_step=pairs_per_step, gmres_iterations=iters[-1],
+                           E_sol=(E.tolist() if batched else E)),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "gmres": gm, "accuracy": acc,
         }
@@ -360,6 +422,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c2l6", "c3", "c5", "c4"], default="c2l6")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain GMRES comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-rows", type=int, default=1024)

@@ -226,6 +226,11 @@ int hobi_solve_batch(hobi_batch_t b, double tol, int32_t max_it, double* phi, do
 /* Solvation energy of every molecule (Eq. solvation_energy), e_sol[n_mol] HOST, kcal/mol. */
 int hobi_energy_batch(hobi_batch_t b, double* e_sol);
 
+/* Timing of the batched far-field launches, as hobi_profile_enable / hobi_profile_read
+ * (pairs counts only the molecules still iterating at each launch). */
+int hobi_batch_profile_enable(hobi_batch_t b, int32_t on);
+int hobi_batch_profile_read(hobi_batch_t b, double* farfield_ms, int64_t* launches, double* pairs);
+
 /* CUDA kernels launched by the batch handle and its per-molecule tables since setup. */
 int hobi_batch_kernel_launches(hobi_batch_t b, int64_t* n);
 

@@ -909,10 +909,32 @@ struct hobi_batch_ctx {
   MolState* ms = nullptr;
   BatchState* gs_host = nullptr;  // pinned
   MolState* ms_host = nullptr;    // pinned
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][profiling]
   bool capturing = false, have_solution = false;
   int64_t launches = 0;
   int ff_grid[2] = {1, 1};
+  // far-field timing (events around each launch; external event nodes inside captured graphs)
+  bool prof = false, prof_pending = false;
+  cudaEvent_t pev[2] = {nullptr, nullptr};
+  double prof_ms = 0.0, prof_pairs = 0.0, pairs_pending = 0.0;
+  int64_t prof_launches = 0;
+  // pair evaluations of one batched far-field launch over the molecules still iterating
+  double active_pairs() const {
+    double p = 0.0;
+    for (int i = 0; i < nmol; ++i)
+      if (!ms_host || (!ms_host[i].converged && !ms_host[i].breakdown)) p += (double)mols_h[i].nv * mols_h[i].n_nodes;
+    return p;
+  }
+  int prof_collect() {
+    if (!prof_pending) return HOBI_OK;
+    float ms = 0.f;
+    HOBI_CK(cudaEventElapsedTime(&ms, pev[0], pev[1]));
+    prof_ms += ms;
+    prof_launches += 1;
+    prof_pairs += pairs_pending;
+    prof_pending = false;
+    return HOBI_OK;
+  }
 
   template <class T>
   int alloc(T** p, size_t count) {
@@ -944,11 +966,30 @@ struct hobi_batch_ctx {
   int matvec(const double* u, const int* kptr, int64_t ld, double* Au, const MolState* mask) {
     const bool fp32 = precision == HOBI_FP32_BULK;
     HOBI_CK(launch_gather_batch(fp32, mols, nmol, node_off, total_nodes, u, kptr, ld, mask, stream));
+    if (prof) {
+      for (auto& e : pev)
+        if (!e) HOBI_CK(cudaEventCreate(&e));
+      HOBI_CK(cudaEventRecordWithFlags(pev[0], stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+    }
     HOBI_CK(launch_farfield_batch(fp32, mols, tasks[fp32], ntasks[fp32], counter, mask, eps, kappa, ff_grid[fp32],
                                   stream));
+    if (prof) {
+      HOBI_CK(cudaEventRecordWithFlags(pev[1], stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+      if (!capturing) {
+        // timed below once the stream has reached the end event
+        pairs_pending = mask ? active_pairs() : active_pairs_all();
+        prof_pending = true;
+      }
+    }
     HOBI_CK(launch_combine_batch(mols, nmol, vert_off, total_verts, u, kptr, ld, Au, mask, stream));
     if (!capturing) launches += 3;
     return HOBI_OK;
+  }
+
+  double active_pairs_all() const {
+    double p = 0.0;
+    for (int i = 0; i < nmol; ++i) p += (double)mols_h[i].nv * mols_h[i].n_nodes;
+    return p;
   }
 
   static constexpr int kIterationKernels = 14;
@@ -971,7 +1012,8 @@ struct hobi_batch_ctx {
   int run_iteration() {
     const int pi = precision == HOBI_FP32_BULK;
     if (!use_graph) return iteration();
-    if (!graph[pi]) {
+    cudaGraphExec_t& gx = graph[pi][prof ? 1 : 0];
+    if (!gx) {
       cudaGraph_t gr = nullptr;
       HOBI_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
       capturing = true;
@@ -983,19 +1025,25 @@ struct hobi_batch_ctx {
         return r;
       }
       if (e != cudaSuccess) return fail(HOBI_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&graph[pi], gr, 0);
+      e = cudaGraphInstantiate(&gx, gr, 0);
       cudaGraphDestroy(gr);
       if (e != cudaSuccess) {
-        graph[pi] = nullptr;
+        gx = nullptr;
         return fail(HOBI_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
       }
     }
-    HOBI_CK(cudaGraphLaunch(graph[pi], stream));
+    if (prof) {
+      pairs_pending = active_pairs();  // molecules active when this replay starts
+      prof_pending = true;
+    }
+    HOBI_CK(cudaGraphLaunch(gx, stream));
     launches += kIterationKernels;
     return HOBI_OK;
   }
   int read_state() {
     HOBI_CK(cudaMemcpyAsync(gs_host, gs, sizeof(BatchState), cudaMemcpyDeviceToHost, stream));
+    HOBI_CK(cudaStreamSynchronize(stream));
+    HOBI_TRY(prof_collect());
     HOBI_CK(cudaMemcpyAsync(ms_host, ms, sizeof(MolState) * nmol, cudaMemcpyDeviceToHost, stream));
     HOBI_CK(cudaStreamSynchronize(stream));
     return HOBI_OK;
@@ -1015,8 +1063,11 @@ struct hobi_batch_ctx {
 
   ~hobi_batch_ctx() {
     if (stream) cudaStreamSynchronize(stream);
-    for (auto& gx : graph)
-      if (gx) cudaGraphExecDestroy(gx);
+    for (auto& row : graph)
+      for (auto& gx : row)
+        if (gx) cudaGraphExecDestroy(gx);
+    for (cudaEvent_t e : pev)
+      if (e) cudaEventDestroy(e);
     for (void* p : allocs)
       if (p) cudaFree(p);
     for (hobi_t s : subs)
@@ -1244,6 +1295,7 @@ int hobi_matvec_batch(hobi_batch_t B, const double* u, double* Au) {
   if (!B->mem_device) HOBI_CK(cudaMemcpyAsync(Au, ad, sizeof(double) * B->N, cudaMemcpyDeviceToHost, B->stream));
   HOBI_TRY(B->leave());
   HOBI_CK(cudaStreamSynchronize(B->stream));
+  HOBI_TRY(B->prof_collect());
   return HOBI_OK;
 }
 
@@ -1345,6 +1397,23 @@ int hobi_energy_batch(hobi_batch_t B, double* e_sol) {
     HOBI_TRY(hobi_energy(h, &e_sol[i]));
     B->launches += h->nc > 0 ? 4 : 0;
   }
+  return HOBI_OK;
+}
+
+int hobi_batch_profile_enable(hobi_batch_t B, int32_t on) {
+  if (!B) return fail(HOBI_ERR_ARG, "NULL handle");
+  B->prof = on != 0;
+  return HOBI_OK;
+}
+
+int hobi_batch_profile_read(hobi_batch_t B, double* farfield_ms, int64_t* launches, double* pairs) {
+  if (!B) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (farfield_ms) *farfield_ms = B->prof_ms;
+  if (launches) *launches = B->prof_launches;
+  if (pairs) *pairs = B->prof_pairs;
+  B->prof_ms = 0.0;
+  B->prof_launches = 0;
+  B->prof_pairs = 0.0;
   return HOBI_OK;
 }
 

@@ -37,6 +37,7 @@ EXPORTS = [
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
     "hobi_matvec_batch", "hobi_solve_batch", "hobi_energy_batch", "hobi_batch_kernel_launches", "hobi_destroy_batch",
+    "hobi_batch_profile_enable", "hobi_batch_profile_read",
 ]
 
 
@@ -99,6 +100,8 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_solve_batch.argtypes = [vp, C.c_double, C.c_int32, dp, dp, dp, dp, C.POINTER(SolveInfo)]
     lib.hobi_energy_batch.argtypes = [vp, dp]
     lib.hobi_batch_kernel_launches.argtypes = [vp, C.POINTER(i64)]
+    lib.hobi_batch_profile_enable.argtypes = [vp, C.c_int32]
+    lib.hobi_batch_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(C.c_double)]
     lib.hobi_destroy_batch.argtypes = [vp]
     lib.hobi_destroy_batch.restype = None
     lib.hobi_last_error.argtypes = []
@@ -308,7 +311,8 @@ class BatchSolver:
     """
 
     def __init__(self, molecules, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
-                 restart: int = 50, use_graph: bool = True, device_mode: bool = False, stream=None):
+                 restart: int = 50, use_graph: bool = True, device_mode: bool = False, stream=None,
+                 device_arrays=None):
         lib = load_library()
         self._lib = lib
         V = np.ascontiguousarray(np.concatenate([m[0] for m in molecules]), dtype=np.float64)
@@ -322,13 +326,13 @@ class BatchSolver:
                                                           for m in molecules])]).astype(np.int64)
         self.n_mol = len(molecules)
         self.nv_total = int(self.vert_off[-1])
-        self.device_mode = device_mode
+        self.device_mode = device_mode or device_arrays is not None
         opt = Options()
         lib.hobi_default_options(C.byref(opt))
         opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
         opt.restart = int(restart)
         opt.use_graph = 1 if use_graph else 0
-        if device_mode:
+        if self.device_mode:
             import torch
 
             dev = torch.device("cuda", torch.cuda.current_device())
@@ -336,7 +340,10 @@ class BatchSolver:
             opt.mem_device = 1
             s = stream if stream is not None else torch.cuda.current_stream(dev)
             opt.stream = C.c_void_p(s.cuda_stream)
-            self._keep = [torch.as_tensor(a, device=dev) for a in (V, F, N, Q)]
+            if device_arrays is not None:  # the concatenated inputs, already resident on the GPU
+                self._keep = [t.contiguous() for t in device_arrays]
+            else:
+                self._keep = [torch.as_tensor(a, device=dev) for a in (V, F, N, Q)]
             ptrs = [t.data_ptr() for t in self._keep]
         else:
             opt.device = -1
@@ -414,3 +421,12 @@ class BatchSolver:
         n = C.c_int64()
         _check(self._lib.hobi_batch_kernel_launches(self._h, C.byref(n)))
         return int(n.value)
+
+    def profile_enable(self, on: bool = True):
+        _check(self._lib.hobi_batch_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        ms, pairs = C.c_double(), C.c_double()
+        n = C.c_int64()
+        _check(self._lib.hobi_batch_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(pairs)))
+        return {"farfield_ms": ms.value, "launches": n.value, "pairs": pairs.value}
