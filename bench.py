@@ -119,6 +119,19 @@ def _dist():
     return ws, rank, local
 
 
+def gather_rank_times(total_ms: float, world_size: int, device=None) -> list[float]:
+    """Every rank's timed-region total (ms), via all_gather on the default process group."""
+    if world_size <= 1:
+        return [total_ms]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    gathered = [torch.zeros_like(t) for _ in range(world_size)]
+    dist.all_gather(gathered, t)
+    return [float(g.item()) for g in gathered]
+
+
 def aggregate(per_rank_total_ms: list[float], pairs_per_step: float, steps: int) -> tuple[float, float]:
     """Whole-job throughput: all ranks' pairs over the slowest rank's time."""
     t = max(per_rank_total_ms)
@@ -311,12 +324,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     total_ms = sum(times)
-    per_rank = [total_ms]
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        gathered = [torch.zeros_like(t) for _ in range(ws)]
-        torch.distributed.all_gather(gathered, t)
-        per_rank = [float(g.item()) for g in gathered]
+    per_rank = gather_rank_times(total_ms, ws, dev)
     pairs_per_step = statistics.mean(pairs_step)
     value, ms_per_step = aggregate(per_rank, pairs_per_step, args.steps)
 
