@@ -66,6 +66,14 @@ def _load():
     lib.or_gmres.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, dp, dp,
                              C.POINTER(C.c_int)]
     lib.or_gmres.restype = C.c_int
+    lib.or_lobi_geometry.argtypes = [C.c_void_p, dp, dp, dp]
+    lib.or_lobi_matvec.argtypes = [C.c_void_p, dp, dp]
+    lib.or_lobi_matvec_rows.argtypes = [C.c_void_p, dp, lp, C.c_int64, dp]
+    lib.or_lobi_rhs.argtypes = [C.c_void_p, dp]
+    lib.or_lobi_energy.argtypes = [C.c_void_p, dp]
+    lib.or_lobi_energy.restype = C.c_double
+    lib.or_lobi_gmres.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, dp, dp, C.POINTER(C.c_int)]
+    lib.or_lobi_gmres.restype = C.c_int
     lib.or_regular_rule.argtypes = [dp, dp, dp]
     lib.or_gauss_legendre4.argtypes = [dp, dp]
     lib.or_singular_rule.argtypes = [dp, dp, dp]
@@ -278,6 +286,59 @@ class Problem:
         conv = C.c_int(0)
         it = _lib.or_gmres(self._h, _p(b), float(tol), int(max_it), int(restart), _p(x), _p(hist),
                            C.byref(conv))
+        return x, int(it), bool(conv.value), hist[: it + 1].copy()
+
+
+class LobiProblem(Problem):
+    """The low-order LOBI-PB scheme (Sec. 2.4) on the same inputs: flat triangles, centroid
+    collocation, self triangle dropped; 2 N_f unknowns (phi then dphi/dnu at centroids)."""
+
+    def geometry(self):
+        x, n, A = np.zeros((self.nf, 3)), np.zeros((self.nf, 3)), np.zeros(self.nf)
+        _lib.or_lobi_geometry(self._h, _p(x), _p(n), _p(A))
+        return x, n, A
+
+    def rhs(self) -> np.ndarray:
+        b = np.zeros(2 * self.nf)
+        _lib.or_lobi_rhs(self._h, _p(b))
+        return b
+
+    def matvec(self, u) -> np.ndarray:
+        u = _f64(u)
+        assert u.shape == (2 * self.nf,)
+        out = np.zeros(2 * self.nf)
+        _lib.or_lobi_matvec(self._h, _p(u), _p(out))
+        return out
+
+    def matvec_rows(self, u, rows):
+        u = _f64(u)
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.zeros((rows.size, 2))
+        _lib.or_lobi_matvec_rows(self._h, _p(u), _p(rows, C.c_int64), rows.size, _p(out))
+        return out[:, 0].copy(), out[:, 1].copy()
+
+    def dense(self) -> np.ndarray:
+        n = 2 * self.nf
+        A = np.zeros((n, n))
+        e = np.zeros(n)
+        for k in range(n):
+            e[:] = 0.0
+            e[k] = 1.0
+            A[:, k] = self.matvec(e)
+        return A
+
+    def energy(self, u) -> float:
+        return float(_lib.or_lobi_energy(self._h, _p(_f64(u))))
+
+    def gmres(self, tol: float = 1e-6, max_it: int = 200, restart: int = 50, b=None):
+        if b is None:
+            b = self.rhs()
+        b = _f64(b)
+        x = np.zeros(2 * self.nf)
+        hist = np.zeros(max_it + 1)
+        conv = C.c_int(0)
+        it = _lib.or_lobi_gmres(self._h, _p(b), float(tol), int(max_it), int(restart), _p(x), _p(hist),
+                                C.byref(conv))
         return x, int(it), bool(conv.value), hist[: it + 1].copy()
 
 

@@ -543,13 +543,14 @@ double or_energy(const or_ctx* c, const double* u) {
 /* ------------------------------------------------------------------ */
 /* GMRES (restarted, modified Gram-Schmidt, Givens rotations)          */
 /* ------------------------------------------------------------------ */
-/* Solves A x = b from x0 = 0; stops when ||b - A x||_2 / ||b||_2 <= tol (the
- * Givens residual estimate) or after max_it matvecs. Returns the iteration
- * count; resid[k] (if non-NULL, length max_it+1) holds the relative residual
- * estimate after k iterations. */
-int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int restart, double* x,
-             double* resid, int* converged) {
-  const int64_t n = 2 * c->nv;
+/* Solves A x = b (n unknowns, A applied by op) from x0 = 0; stops when
+ * ||b - A x||_2 / ||b||_2 <= tol (the Givens residual estimate) or after max_it
+ * matvecs. Returns the iteration count; resid[k] (if non-NULL, length max_it+1)
+ * holds the relative residual estimate after k iterations. */
+typedef void (*or_operator)(const or_ctx* c, const double* u, double* Au);
+
+static int gmres_core(const or_ctx* c, or_operator op, int64_t n, const double* b, double tol, int max_it,
+                      int restart, double* x, double* resid, int* converged) {
   int m = restart;
   double* Vb = (double*)malloc(sizeof(double) * n * (m + 1));
   double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));
@@ -568,7 +569,7 @@ int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int resta
   if (bnorm == 0.0) { *converged = 1; goto done; }
   while (it < max_it) {
     /* r = b - A x */
-    or_matvec(c, x, w);
+    op(c, x, w);
     double beta = 0.0;
     for (int64_t i = 0; i < n; ++i) { w[i] = b[i] - w[i]; beta += w[i] * w[i]; }
     beta = sqrt(beta);
@@ -578,7 +579,7 @@ int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int resta
     g[0] = beta;
     int k;
     for (k = 0; k < m && it < max_it; ++k) {
-      or_matvec(c, &Vb[n * k], w);
+      op(c, &Vb[n * k], w);
       ++it;
       for (int jj = 0; jj <= k; ++jj) {
         double h = 0.0;
@@ -623,6 +624,109 @@ int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int resta
 done:
   free(Vb); free(H); free(cs); free(sn); free(g); free(w); free(y);
   return it;
+}
+
+int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int restart, double* x, double* resid,
+             int* converged) {
+  return gmres_core(c, or_matvec, 2 * c->nv, b, tol, max_it, restart, x, resid, converged);
+}
+
+/* ------------------------------------------------------------------ */
+/* Low-order scheme, LOBI-PB (Sec. 2.4, eqdbef1/eqdbef2)               */
+/* ------------------------------------------------------------------ */
+/* Flat triangles with centroid collocation: unknowns are phi and dphi/dnu at the
+ * N_f centroids, each triangle contributes W_j = its area times the kernels at its
+ * centroid, and the singular (self) triangle j = i is dropped. Normals are the flat
+ * face normals. */
+static void lobi_face(const or_ctx* c, int64_t j, double* x, double* n, double* A) {
+  const int32_t* f = &c->F[3 * j];
+  const double *a = &c->V[3 * f[0]], *b = &c->V[3 * f[1]], *d = &c->V[3 * f[2]];
+  double e1[3], e2[3];
+  for (int k = 0; k < 3; ++k) {
+    x[k] = (a[k] + b[k] + d[k]) / 3.0;
+    e1[k] = b[k] - a[k];
+    e2[k] = d[k] - a[k];
+  }
+  cross3(e1, e2, n);
+  double len = norm3(n);
+  *A = 0.5 * len;
+  n[0] /= len; n[1] /= len; n[2] /= len;
+}
+
+void or_lobi_geometry(const or_ctx* c, double* x, double* n, double* A) {
+  for (int64_t j = 0; j < c->nf; ++j) lobi_face(c, j, &x[3 * j], &n[3 * j], &A[j]);
+}
+
+static void lobi_row(const or_ctx* c, const double* u, int64_t i, double* out1, double* out2) {
+  const int64_t nf = c->nf;
+  double xi[3], ni[3], Ai;
+  lobi_face(c, i, xi, ni, &Ai);
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t j = 0; j < nf; ++j) {
+    if (j == i) continue; /* the singular triangle is removed */
+    double xj[3], nj[3], Aj, K[4];
+    lobi_face(c, j, xj, nj, &Aj);
+    or_kernels(xi, ni, xj, nj, c->eps, c->kappa, K);
+    s1 += Aj * (K[0] * u[nf + j] + K[1] * u[j]);
+    s2 += Aj * (K[2] * u[nf + j] + K[3] * u[j]);
+  }
+  *out1 = 0.5 * (1.0 + c->eps) * u[i] - s1;
+  *out2 = 0.5 * (1.0 + 1.0 / c->eps) * u[nf + i] - s2;
+}
+
+void or_lobi_matvec(const or_ctx* c, const double* u, double* Au) {
+  const int64_t nf = c->nf;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t i = 0; i < nf; ++i) lobi_row(c, u, i, &Au[i], &Au[nf + i]);
+}
+
+void or_lobi_matvec_rows(const or_ctx* c, const double* u, const int64_t* rows, int64_t nrows, double* out) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < nrows; ++k) lobi_row(c, u, rows[k], &out[2 * k], &out[2 * k + 1]);
+}
+
+/* Sources S1, S2 (Eq_Ss, with 1/eps1) at the centroids, face normals. */
+void or_lobi_rhs(const or_ctx* c, double* b) {
+  const int64_t nf = c->nf;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nf; ++i) {
+    double x[3], nx[3], A;
+    lobi_face(c, i, x, nx, &A);
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k = 0; k < c->nc; ++k) {
+      const double* q = &c->Qc[4 * k];
+      double d[3] = {x[0] - q[0], x[1] - q[1], x[2] - q[2]};
+      double r = norm3(d);
+      s1 += q[3] / (4.0 * OR_PI * c->eps1 * r);
+      s2 += -q[3] * dot3(d, nx) / (4.0 * OR_PI * c->eps1 * r * r * r);
+    }
+    b[i] = s1;
+    b[nf + i] = s2;
+  }
+}
+
+/* E_sol (kcal/mol) with the centroid rule for the reaction potential (solvation_energy). */
+double or_lobi_energy(const or_ctx* c, const double* u) {
+  const int64_t nf = c->nf;
+  double unused_nx[3] = {0.0, 0.0, 1.0}; /* K1, K2 do not use the target normal */
+  double e = 0.0;
+  for (int64_t k = 0; k < c->nc; ++k) {
+    const double* q = &c->Qc[4 * k];
+    double phi = 0.0;
+    for (int64_t j = 0; j < nf; ++j) {
+      double xj[3], nj[3], Aj, K[4];
+      lobi_face(c, j, xj, nj, &Aj);
+      or_kernels(q, unused_nx, xj, nj, c->eps, c->kappa, K);
+      phi += Aj * (K[0] * u[nf + j] + K[1] * u[j]);
+    }
+    e += q[3] * phi;
+  }
+  return 0.5 * 4.0 * OR_PI * 332.0716 * e;
+}
+
+int or_lobi_gmres(const or_ctx* c, const double* b, double tol, int max_it, int restart, double* x, double* resid,
+                  int* converged) {
+  return gmres_core(c, or_lobi_matvec, 2 * c->nf, b, tol, max_it, restart, x, resid, converged);
 }
 
 int or_num_threads(void) {
