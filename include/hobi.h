@@ -16,7 +16,9 @@
  *    ABI. On failure, hobi_last_error() returns a message (thread-local).
  *  - Units: lengths in Angstrom, charges in e, kappa in 1/Angstrom. The
  *    unknowns u = [phi; dphi/dnu] (2 N_v doubles: the N_v vertex potentials,
- *    then the N_v normal derivatives on the inside of the surface) are in the
+ *    then the N_v normal derivatives on the inside of the surface; with the LOBI-PB
+ *    scheme the collocation points are the N_f face centroids instead, and every "n_v"
+ *    below reads n_f) are in the
  *    units of the formulation (G = 1/(4 pi r)); multiply by HOBI_KCAL_PER_MOL_E
  *    for kcal/(mol e). Energies are kcal/mol.
  *  - Dielectric ratio: eps = eps2/eps1 (the paper prints eps1/eps2 after
@@ -63,6 +65,15 @@ typedef enum {
                          setup, the singular-triangle correction, GMRES and the energy sum */
 } hobi_precision;
 
+typedef enum {
+  HOBI_SCHEME_HOBI = 0, /* curved elements, 4-point regular + 16-point singular rules, unknowns at the
+                           N_v vertices (Sec. 2.2-2.3) */
+  HOBI_SCHEME_LOBI = 1  /* the paper's low-order comparison scheme LOBI-PB (Sec. 2.4, Eqs.
+                           eqdbef1/eqdbef2): flat triangles, centroid collocation, the singular
+                           (self) triangle dropped; unknowns at the N_f centroids, normals are the
+                           flat face normals (vertex_normals are only validated) */
+} hobi_scheme;
+
 typedef struct {
   int32_t precision;  /* hobi_precision (default HOBI_FP32_BULK) */
   int32_t mem_device; /* 0: array arguments are host pointers; 1: device pointers */
@@ -70,6 +81,7 @@ typedef struct {
   int32_t restart;    /* GMRES restart length m (default 50, max 200) */
   int32_t use_graph;  /* 1 (default): replay each GMRES iteration as a captured CUDA graph */
   int32_t device;     /* CUDA device ordinal; -1 (default): the current device */
+  int32_t scheme;     /* hobi_scheme (default HOBI_SCHEME_HOBI); the batch API accepts HOBI only */
 } hobi_options;
 
 typedef struct {
@@ -107,8 +119,10 @@ int hobi_setup(const double* vertices, int64_t n_v, const int32_t* faces, int64_
 /* Switch the far-field precision of later matvec/solve/energy calls (hobi_precision). */
 int hobi_set_precision(hobi_t h, int32_t precision);
 
-/* Sizes of the problem (any output pointer may be NULL). n_nodes = 4 n_f quadrature nodes. */
-int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_nodes);
+/* Sizes of the problem (any output pointer may be NULL). n_points: collocation points, i.e.
+ * the length of phi / dphi and half the length of u (N_v for HOBI, N_f for LOBI); n_nodes:
+ * source quadrature nodes (4 N_f for HOBI, N_f for LOBI). */
+int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_nodes, int64_t* n_points);
 
 /* One discrete operator application Au = A u (Eqs. eqdbef3-eqdbef6): u and Au are 2 n_v
  * doubles (layout above). Au must not alias u. */

@@ -31,8 +31,9 @@ __device__ __forceinline__ float2 pair_of(float a) { return make_float2(a, a); }
 
 // One block's share of the FP32 far field: targets bx*1024 .. bx*1024+1023 (4 per thread)
 // against source tiles [t0, t1); results (FP64) to out[i] (row 1) and out[nt + i] (row 2).
-// sh: 4 kTile float4 of shared memory.
-template <bool ROW2>
+// sh: 4 kTile float4 of shared memory. SKIP_SELF: a pair at zero distance (a collocation point
+// that is also a source node, LOBI-PB) contributes nothing.
+template <bool ROW2, bool SKIP_SELF = false>
 __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src,
                                            int t0, int t1, float neg_kl2e, float kap, float eps,
                                            double* __restrict__ out, int bx, float4* sh) {
@@ -73,7 +74,11 @@ __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int n
       for (int k = 0; k < TP; ++k) {
         const float2 dx = __fadd2_rn(px[k], nyx), dy = __fadd2_rn(py[k], nyy), dz = __fadd2_rn(pz[k], nyz);
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        if (SKIP_SELF) {  // 1/r -> 0 before r is formed: every term of the pair then vanishes
+          ir.x = r2.x > 0.f ? ir.x : 0.f;
+          ir.y = r2.y > 0.f ? ir.y : 0.f;
+        }
         const float2 r = __fmul2_rn(r2, ir);
         const float2 ea = __fmul2_rn(nk2, r);
         const float2 E = make_float2(exp2_approx(ea.x), exp2_approx(ea.y));
@@ -121,7 +126,7 @@ __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int n
 }
 
 // One block's share of the FP64 far field (2 targets per thread); sh: 4 kTile double2.
-template <bool ROW2>
+template <bool ROW2, bool SKIP_SELF = false>
 __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int nt, const double* __restrict__ src,
                                            int t0, int t1, double kap, double eps, double ieps,
                                            double* __restrict__ out, int bx, double2* sh) {
@@ -148,7 +153,7 @@ __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int n
         double dx = px[k] - y01.x, dy = py[k] - y01.y, dz = pz[k] - y2s.x;
         double r2 = dx * dx + dy * dy + dz * dz;
         double r = sqrt(r2);
-        double ir = 1.0 / r;
+        double ir = (SKIP_SELF && !(r2 > 0.0)) ? 0.0 : 1.0 / r;
         double kr = kap * r;
         double E = exp(-kr);
         double P = E * (1.0 + kr);
@@ -212,6 +217,45 @@ __device__ __forceinline__ void gather64_node(int node, int nv, const int* __res
   const double* y = ny + 3 * (size_t)node;
   const double* n = nnu + 3 * (size_t)node;
   double* o = src + 8 * (size_t)node;
+  o[0] = y[0] - center[0];
+  o[1] = y[1] - center[1];
+  o[2] = y[2] - center[2];
+  o[3] = sig;
+  o[4] = mu * n[0];
+  o[5] = mu * n[1];
+  o[6] = mu * n[2];
+  o[7] = 0.0;
+}
+
+// LOBI-PB node = face j: centroid y_j, face normal nu_j, weight A_j (area), densities from the
+// centroid unknowns u_j, u_{N_f+j} (Sec. 2.4, eqdbef1/eqdbef2).
+__device__ __forceinline__ void gather32_lobi(int j, int nf, const double* __restrict__ ny,
+                                              const double* __restrict__ nnu, const double* __restrict__ nW,
+                                              const double* __restrict__ center, const double* __restrict__ u,
+                                              double inv_eps, float4* __restrict__ src) {
+  const double A = nW[3 * (size_t)j];
+  const double sig = A * u[nf + j] * kInv4Pi, mu = A * u[j] * kInv4Pi;
+  const double* y = ny + 3 * (size_t)j;
+  const double* n = nnu + 3 * (size_t)j;
+  const float yx = (float)(center[0] - y[0]), yy = (float)(center[1] - y[1]), yz = (float)(center[2] - y[2]);
+  const float sg = (float)sig, se = (float)(sig * inv_eps);
+  const float mx = (float)(mu * n[0]), my = (float)(mu * n[1]), mz = (float)(mu * n[2]);
+  float4* o = src + 4 * (size_t)j;
+  o[0] = make_float4(yx, yx, yy, yy);
+  o[1] = make_float4(yz, yz, sg, sg);
+  o[2] = make_float4(mx, mx, my, my);
+  o[3] = make_float4(mz, mz, se, se);
+}
+
+__device__ __forceinline__ void gather64_lobi(int j, int nf, const double* __restrict__ ny,
+                                              const double* __restrict__ nnu, const double* __restrict__ nW,
+                                              const double* __restrict__ center, const double* __restrict__ u,
+                                              double* __restrict__ src) {
+  const double A = nW[3 * (size_t)j];
+  const double sig = A * u[nf + j] * kInv4Pi, mu = A * u[j] * kInv4Pi;
+  const double* y = ny + 3 * (size_t)j;
+  const double* n = nnu + 3 * (size_t)j;
+  double* o = src + 8 * (size_t)j;
   o[0] = y[0] - center[0];
   o[1] = y[1] - center[1];
   o[2] = y[2] - center[2];

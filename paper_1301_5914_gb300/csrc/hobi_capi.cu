@@ -55,8 +55,10 @@ struct hobi_ctx {
   cudaStream_t user_stream = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
-  int mem_device = 0, precision = HOBI_FP32_BULK, restart = 50, use_graph = 1;
-  int64_t nv = 0, nf = 0, nc = 0, n_nodes = 0, n_pad = 0;
+  int mem_device = 0, precision = HOBI_FP32_BULK, restart = 50, use_graph = 1, scheme = HOBI_SCHEME_HOBI;
+  // nv: collocation points (mesh vertices for HOBI, face centroids for LOBI); nv_mesh: mesh vertices
+  int64_t nv = 0, nf = 0, nc = 0, n_nodes = 0, n_pad = 0, nv_mesh = 0;
+  int* zero_ptr = nullptr;  // LOBI: an all-zero incidence row pointer (no singular correction)
   double eps1 = 1, eps2 = 80, kappa = 0, eps = 80;
   int num_sms = 1;
   std::vector<void*> allocs;
@@ -156,14 +158,15 @@ struct hobi_ctx {
   }
 
   // --------------------------------------------------------------- matvec pipeline
-  int farfield(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, double* out) {
+  int farfield(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, double* out,
+               bool skip_self = false) {
     cudaEvent_t a = nullptr, bb = nullptr;
     if (prof && capturing) {
       const int pi = fp32 ? 1 : 0;
       for (int q = 0; q < 2; ++q)
         if (!gev[pi][q]) HOBI_CK(cudaEventCreate(&gev[pi][q]));
       HOBI_CK(cudaEventRecordWithFlags(gev[pi][0], stream, cudaEventRecordExternal));
-      HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream));
+      HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream, skip_self));
       HOBI_CK(cudaEventRecordWithFlags(gev[pi][1], stream, cudaEventRecordExternal));
       graph_pairs[pi] = (double)p.n_targets * (double)n_nodes;
       return HOBI_OK;
@@ -180,7 +183,7 @@ struct hobi_ctx {
       ++prof_used;
       HOBI_CK(cudaEventRecord(a, stream));
     }
-    HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream));
+    HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream, skip_self));
     if (prof) {
       HOBI_CK(cudaEventRecord(bb, stream));
       pending_pairs += (double)p.n_targets * (double)n_nodes;
@@ -188,14 +191,24 @@ struct hobi_ctx {
     return HOBI_OK;
   }
 
+  // node densities of u (scheme-dependent node layout)
+  int gather(bool fp32, const double* u, const int* kptr, int64_t ld) {
+    if (scheme == HOBI_SCHEME_LOBI)
+      HOBI_CK(launch_gather_lobi(fp32, (int)nf, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps, src32, src64, stream));
+    else
+      HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps,
+                            src32, src64, stream));
+    return HOBI_OK;
+  }
+
   // Au = A u with u = base + (*kptr) * ld when kptr is given (device pointers)
   int matvec_dev(const double* u, const int* kptr, int64_t ld, double* Au) {
     const bool fp32 = precision == HOBI_FP32_BULK;
-    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps,
-                          src32, src64, stream));
-    HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part));
-    HOBI_CK(launch_combine((int)nv, plan[fp32].chunks, part, F, inc_ptr, inc_face, corr, eps, u, kptr, ld, Au,
-                           stream));
+    const bool lobi = scheme == HOBI_SCHEME_LOBI;
+    HOBI_TRY(gather(fp32, u, kptr, ld));
+    HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part, lobi));
+    HOBI_CK(launch_combine((int)nv, plan[fp32].chunks, part, F, lobi ? zero_ptr : inc_ptr, inc_face, corr, eps, u,
+                           kptr, ld, Au, stream));
     if (!capturing) launches += 3;
     return HOBI_OK;
   }
@@ -308,8 +321,7 @@ struct hobi_ctx {
     const bool fp32 = precision == HOBI_FP32_BULK;
     FarFieldPlan p = plan_farfield(fp32, (int)np, (int)n_pad, false, num_sms, farfield_blocks_per_sm(fp32, false));
     HOBI_TRY(ensure_ppart((size_t)p.chunks * (size_t)np));
-    HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)n_pad, (int)nv, F, ny, nnu, nW, center, x, nullptr, 0, 1.0 / eps,
-                          src32, src64, stream));
+    HOBI_TRY(gather(fp32, x, nullptr, 0));
     HOBI_TRY(farfield(fp32, p, t32, t64, ppart));
     HOBI_CK(launch_reduce_points((int)np, p.chunks, ppart, phi, stream));
     launches += 3;
@@ -391,36 +403,62 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   if (flags == kBadCharge) return fail(HOBI_ERR_ARG, "non-finite charge position or value");
   if (flags) return fail(HOBI_ERR_MESH, mesh_message(flags));
 
-  // curved elements, nodes, correction, right-hand side (Sec. 2.6 routines (1)-(4))
-  h->n_nodes = 4 * nf;
-  h->n_pad = (h->n_nodes + kTile - 1) / kTile * kTile;
-  HOBI_TRY(h->alloc(&h->elem, 30 * nf));
-  HOBI_TRY(h->alloc(&h->ny, 3 * h->n_nodes));
-  HOBI_TRY(h->alloc(&h->nnu, 3 * h->n_nodes));
-  HOBI_TRY(h->alloc(&h->nW, 3 * h->n_nodes));
-  HOBI_TRY(h->alloc(&h->corr, 12 * 3 * nf));
-  HOBI_TRY(h->alloc(&h->b, 2 * nv));
-  HOBI_TRY(h->alloc(&h->tgt32, 2 * nv));
-  HOBI_TRY(h->alloc(&h->tgt64, 8 * nv));
-  HOBI_TRY(h->alloc(&h->ctgt32, 2 * (nc > 0 ? nc : 1)));
-  HOBI_TRY(h->alloc(&h->ctgt64, 8 * (nc > 0 ? nc : 1)));
-  HOBI_TRY(h->alloc(&h->src32, 4 * h->n_pad));
-  HOBI_TRY(h->alloc(&h->src64, 8 * h->n_pad));
-  HOBI_CK(launch_node_gen((int)nf, h->F, h->V, h->Nv, h->elem, h->ny, h->nnu, h->nW, h->flags, h->stream));
-  HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem, h->ny,
-                                    h->nnu, h->nW, h->eps, h->kappa, h->corr, h->stream));
-  HOBI_CK(launch_rhs((int)nv, (int)nc, h->V, h->Nv, h->Q, h->eps1, h->b, h->stream));
-  HOBI_CK(launch_targets((int)nv, h->V, h->Nv, h->center, h->tgt32, h->tgt64, h->stream));
-  HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
-  HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
-  h->launches += 4 + (nc > 0 ? 1 : 0) + (h->n_pad > h->n_nodes ? 1 : 0);
+  h->nv_mesh = nv;
+  if (h->scheme == HOBI_SCHEME_LOBI) {
+    // LOBI-PB (Sec. 2.4): one node per flat face at its centroid; collocation at the centroids
+    h->nv = nf;
+    h->n_nodes = nf;
+    h->n_pad = (h->n_nodes + kTile - 1) / kTile * kTile;
+    HOBI_TRY(h->alloc(&h->ny, 3 * nf));
+    HOBI_TRY(h->alloc(&h->nnu, 3 * nf));
+    HOBI_TRY(h->alloc(&h->nW, 3 * nf));
+    HOBI_TRY(h->alloc(&h->zero_ptr, nf + 1));
+    HOBI_TRY(h->alloc(&h->b, 2 * nf));
+    HOBI_TRY(h->alloc(&h->tgt32, 2 * nf));
+    HOBI_TRY(h->alloc(&h->tgt64, 8 * nf));
+    HOBI_TRY(h->alloc(&h->ctgt32, 2 * (nc > 0 ? nc : 1)));
+    HOBI_TRY(h->alloc(&h->ctgt64, 8 * (nc > 0 ? nc : 1)));
+    HOBI_TRY(h->alloc(&h->src32, 4 * h->n_pad));
+    HOBI_TRY(h->alloc(&h->src64, 8 * h->n_pad));
+    HOBI_CK(cudaMemsetAsync(h->zero_ptr, 0, sizeof(int) * (nf + 1), h->stream));
+    HOBI_CK(launch_lobi_geometry((int)nf, h->F, h->V, h->ny, h->nnu, h->nW, h->flags, h->stream));
+    HOBI_CK(launch_rhs((int)nf, (int)nc, h->ny, h->nnu, h->Q, h->eps1, h->b, h->stream));
+    HOBI_CK(launch_targets((int)nf, h->ny, h->nnu, h->center, h->tgt32, h->tgt64, h->stream));
+    HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
+    HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
+    h->launches += 3 + (nc > 0 ? 1 : 0) + (h->n_pad > h->n_nodes ? 1 : 0);
+  } else {
+    // curved elements, nodes, correction, right-hand side (Sec. 2.6 routines (1)-(4))
+    h->n_nodes = 4 * nf;
+    h->n_pad = (h->n_nodes + kTile - 1) / kTile * kTile;
+    HOBI_TRY(h->alloc(&h->elem, 30 * nf));
+    HOBI_TRY(h->alloc(&h->ny, 3 * h->n_nodes));
+    HOBI_TRY(h->alloc(&h->nnu, 3 * h->n_nodes));
+    HOBI_TRY(h->alloc(&h->nW, 3 * h->n_nodes));
+    HOBI_TRY(h->alloc(&h->corr, 12 * 3 * nf));
+    HOBI_TRY(h->alloc(&h->b, 2 * nv));
+    HOBI_TRY(h->alloc(&h->tgt32, 2 * nv));
+    HOBI_TRY(h->alloc(&h->tgt64, 8 * nv));
+    HOBI_TRY(h->alloc(&h->ctgt32, 2 * (nc > 0 ? nc : 1)));
+    HOBI_TRY(h->alloc(&h->ctgt64, 8 * (nc > 0 ? nc : 1)));
+    HOBI_TRY(h->alloc(&h->src32, 4 * h->n_pad));
+    HOBI_TRY(h->alloc(&h->src64, 8 * h->n_pad));
+    HOBI_CK(launch_node_gen((int)nf, h->F, h->V, h->Nv, h->elem, h->ny, h->nnu, h->nW, h->flags, h->stream));
+    HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem, h->ny,
+                                      h->nnu, h->nW, h->eps, h->kappa, h->corr, h->stream));
+    HOBI_CK(launch_rhs((int)nv, (int)nc, h->V, h->Nv, h->Q, h->eps1, h->b, h->stream));
+    HOBI_CK(launch_targets((int)nv, h->V, h->Nv, h->center, h->tgt32, h->tgt64, h->stream));
+    HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
+    HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
+    h->launches += 4 + (nc > 0 ? 1 : 0) + (h->n_pad > h->n_nodes ? 1 : 0);
+  }
   HOBI_CK(cudaMemcpyAsync(&flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HOBI_CK(cudaStreamSynchronize(h->stream));
   if (flags & kDegenerateElement)
     return fail(HOBI_ERR_MESH, "invalid mesh: a curved element has a zero or non-finite area Jacobian "
                                "(vertex normals inconsistent with the faces)");
 
-  HOBI_TRY(h->alloc(&h->x, 2 * nv));
+  HOBI_TRY(h->alloc(&h->x, 2 * h->nv));
   HOBI_TRY(h->alloc(&h->e_dev, 1));
   HOBI_CK(cudaMallocHost(&h->host_scalar, sizeof(double)));
   if (light) {
@@ -430,14 +468,14 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   // far-field plans and partial-sum buffers
   size_t part_elems = 0;
   for (int fp32 = 0; fp32 < 2; ++fp32) {
-    h->plan[fp32] = plan_farfield(fp32, (int)nv, (int)h->n_pad, true, h->num_sms, farfield_blocks_per_sm(fp32, true));
-    size_t need = (size_t)h->plan[fp32].chunks * 2 * nv;
+    h->plan[fp32] = plan_farfield(fp32, (int)h->nv, (int)h->n_pad, true, h->num_sms, farfield_blocks_per_sm(fp32, true));
+    size_t need = (size_t)h->plan[fp32].chunks * 2 * h->nv;
     if (need > part_elems) part_elems = need;
   }
   HOBI_TRY(h->alloc(&h->part, part_elems));
 
   // iterate vectors and GMRES workspace
-  const int64_t n = 2 * nv;
+  const int64_t n = 2 * h->nv;
   const int m = h->restart;
   HOBI_TRY(h->alloc(&h->u_stage, n));
   HOBI_TRY(h->alloc(&h->au_stage, n));
@@ -473,6 +511,7 @@ void hobi_default_options(hobi_options* opt) {
   opt->restart = 50;
   opt->use_graph = 1;
   opt->device = -1;
+  opt->scheme = HOBI_SCHEME_HOBI;
 }
 
 const char* hobi_last_error(void) { return g_err.c_str(); }
@@ -500,6 +539,7 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   hobi_default_options(&o);
   if (opt) o = *opt;
   if (o.precision != HOBI_FP64 && o.precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
+  if (o.scheme != HOBI_SCHEME_HOBI && o.scheme != HOBI_SCHEME_LOBI) return fail(HOBI_ERR_ARG, "unknown scheme");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
 
@@ -516,6 +556,7 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   h->precision = o.precision;
   h->restart = o.restart;
   h->use_graph = o.use_graph ? 1 : 0;
+  h->scheme = o.scheme;
   h->nv = n_v;
   h->nf = n_f;
   h->nc = n_c;
@@ -567,9 +608,10 @@ int hobi_set_precision(hobi_t h, int32_t precision) {
   return HOBI_OK;
 }
 
-int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_nodes) {
+int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_nodes, int64_t* n_points) {
   if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
-  if (n_v) *n_v = h->nv;
+  if (n_points) *n_points = h->nv;
+  if (n_v) *n_v = h->nv_mesh;
   if (n_f) *n_f = h->nf;
   if (n_c) *n_c = h->nc;
   if (n_nodes) *n_nodes = h->n_nodes;
@@ -748,7 +790,8 @@ int hobi_get_nodes(hobi_t h, double* y, double* nu, double* W) {
 
 int hobi_get_correction(hobi_t h, int64_t* n_entries, int32_t* vertex, int32_t* face, double* coeff) {
   if (!h || !n_entries) return fail(HOBI_ERR_ARG, "NULL argument");
-  *n_entries = 3 * h->nf;
+  *n_entries = h->scheme == HOBI_SCHEME_LOBI ? 0 : 3 * h->nf;
+  if (*n_entries == 0) return HOBI_OK;
   if (!vertex && !face && !coeff) return HOBI_OK;
   DeviceGuard guard(h->device);
   HOBI_TRY(h->enter());
@@ -870,8 +913,7 @@ extern "C" int hobi_reaction_potential_noalloc(hobi_t h, const double* points, i
   HOBI_TRY(h->enter());
   HOBI_TRY(h->copy_in(pts, points, 3 * n));
   HOBI_CK(launch_points((int)n, pts, 3, h->center, t32, t64, h->stream));
-  HOBI_CK(launch_gather(fp32, (int)h->n_nodes, (int)h->n_pad, (int)h->nv, h->F, h->ny, h->nnu, h->nW, h->center,
-                        h->x, nullptr, 0, 1.0 / h->eps, h->src32, h->src64, h->stream));
+  HOBI_TRY(h->gather(fp32, h->x, nullptr, 0));
   HOBI_CK(launch_farfield(fp32, p, t32, t64, h->src32, h->src64, h->eps, h->kappa, part, h->stream));
   HOBI_CK(launch_reduce_points((int)n, p.chunks, part, phi_d, h->stream));
   h->launches += 4;
@@ -1216,6 +1258,7 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
   hobi_default_options(&o);
   if (opt) o = *opt;
   if (o.precision != HOBI_FP64 && o.precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
+  if (o.scheme != HOBI_SCHEME_HOBI) return fail(HOBI_ERR_ARG, "the batch API supports the HOBI scheme only");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
   int dev = o.device;

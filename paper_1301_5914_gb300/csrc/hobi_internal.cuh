@@ -63,6 +63,9 @@ cudaError_t launch_correction_entries(int n_entries, const int* vert, const int*
                                       const double* Nv, const int* inc_face, const double* elem, const double* ny,
                                       const double* nnu, const double* nW, double eps, double kappa, double* corr,
                                       cudaStream_t s);
+// LOBI-PB flat-face centroids, unit normals and areas
+cudaError_t launch_lobi_geometry(int nf, const int* F, const double* V, double* ny, double* nnu, double* nW,
+                                 int* flags, cudaStream_t s);
 cudaError_t launch_rhs(int nv, int nc, const double* V, const double* Nv, const double* Q, double eps1,
                        double* b, cudaStream_t s);
 cudaError_t launch_targets(int nv, const double* V, const double* Nv, const double* center, float4* tgt32,
@@ -89,9 +92,14 @@ struct FarFieldPlan {
 FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2, int num_sms,
                            int blocks_per_sm);
 int farfield_blocks_per_sm(bool fp32, bool row2);
+// skip_self: pairs at zero distance contribute nothing (LOBI-PB, where targets are source nodes)
 cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt32, const double* tgt64,
                             const float4* src32, const double* src64, double eps, double kappa,
-                            double* part, cudaStream_t s);
+                            double* part, cudaStream_t s, bool skip_self = false);
+// LOBI-PB node densities (one node per face)
+cudaError_t launch_gather_lobi(bool fp32, int nf, const double* ny, const double* nnu, const double* nW,
+                               const double* center, const double* u, const int* kptr, int64_t ld, double inv_eps,
+                               float4* src32, double* src64, cudaStream_t s);
 // Au = diag u - (sum of chunk partials + singular correction)  (rows i and n_v + i)
 cudaError_t launch_combine(int nv, int chunks, const double* part, const int* F, const int* inc_ptr,
                            const int* inc_face, const double* corr, double eps, const double* u,

@@ -49,6 +49,19 @@ __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const
   ff::gather64_node(node, nv, F, ny, nnu, nW, center, u, src);
 }
 
+__global__ void k_gather_lobi(bool fp32, int nf, const double* __restrict__ ny, const double* __restrict__ nnu,
+                              const double* __restrict__ nW, const double* __restrict__ center,
+                              const double* __restrict__ u, const int* kptr, int64_t ld, double inv_eps,
+                              float4* __restrict__ src32, double* __restrict__ src64) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nf) return;
+  if (kptr) u += (int64_t)(*kptr) * ld;
+  if (fp32)
+    ff::gather32_lobi(j, nf, ny, nnu, nW, center, u, inv_eps, src32);
+  else
+    ff::gather64_lobi(j, nf, ny, nnu, nW, center, u, src64);
+}
+
 // Padding nodes: far away with zero densities, so every term they add is exactly zero.
 __global__ void k_pad(int n_nodes, int n_pad, float4* src32, double* src64) {
   int node = n_nodes + blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,23 +76,23 @@ __global__ void k_pad(int n_nodes, int n_pad, float4* src32, double* src64) {
 }
 
 // ------------------------------------------------------------------ far field kernels
-template <bool ROW2>
+template <bool ROW2, bool SKIP_SELF = false>
 __global__ void __launch_bounds__(kFF32Threads, 2)
     k_farfield32(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src, int n_tiles, int tpc,
                  float neg_kl2e, float kap, float eps, double* __restrict__ part, int64_t ldp) {
   __shared__ float4 sh[4 * kTile];
   const int t0 = blockIdx.y * tpc;
-  ff::ff32_block<ROW2>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), neg_kl2e, kap, eps,
+  ff::ff32_block<ROW2, SKIP_SELF>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), neg_kl2e, kap, eps,
                        part + (size_t)blockIdx.y * ldp, blockIdx.x, sh);
 }
 
-template <bool ROW2>
+template <bool ROW2, bool SKIP_SELF = false>
 __global__ void __launch_bounds__(kFF64Threads)
     k_farfield64(const double* __restrict__ tgt, int nt, const double* __restrict__ src, int n_tiles, int tpc,
                  double kap, double eps, double ieps, double* __restrict__ part, int64_t ldp) {
   __shared__ double2 sh[4 * kTile];
   const int t0 = blockIdx.y * tpc;
-  ff::ff64_block<ROW2>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), kap, eps, ieps, part + (size_t)blockIdx.y * ldp,
+  ff::ff64_block<ROW2, SKIP_SELF>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), kap, eps, ieps, part + (size_t)blockIdx.y * ldp,
                        blockIdx.x, sh);
 }
 
@@ -130,6 +143,13 @@ cudaError_t launch_gather(bool fp32, int n_nodes, int n_pad, int nv, const int* 
     k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, src32);
   else
     k_gather64<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, src64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_lobi(bool fp32, int nf, const double* ny, const double* nnu, const double* nW,
+                               const double* center, const double* u, const int* kptr, int64_t ld, double inv_eps,
+                               float4* src32, double* src64, cudaStream_t s) {
+  k_gather_lobi<<<nblk(nf, 256), 256, 0, s>>>(fp32, nf, ny, nnu, nW, center, u, kptr, ld, inv_eps, src32, src64);
   return cudaGetLastError();
 }
 
@@ -186,12 +206,15 @@ FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2,
 
 cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt32, const double* tgt64,
                             const float4* src32, const double* src64, double eps, double kappa, double* part,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool skip_self) {
   const int64_t ldp = p.row2 ? 2 * (int64_t)p.n_targets : (int64_t)p.n_targets;
   if (fp32) {
     dim3 grid((p.n_targets + kFF32Threads * kFF32Targets - 1) / (kFF32Threads * kFF32Targets), p.chunks);
     const float neg_kl2e = (float)(-kappa * 1.4426950408889634074);
-    if (p.row2)
+    if (p.row2 && skip_self)
+      k_farfield32<true, true><<<grid, kFF32Threads, 0, s>>>(tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk,
+                                                             neg_kl2e, (float)kappa, (float)eps, part, ldp);
+    else if (p.row2)
       k_farfield32<true><<<grid, kFF32Threads, 0, s>>>(tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk,
                                                        neg_kl2e, (float)kappa, (float)eps, part, ldp);
     else
@@ -199,7 +222,10 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
                                                         neg_kl2e, (float)kappa, (float)eps, part, ldp);
   } else {
     dim3 grid((p.n_targets + kFF64Threads * kFF64Targets - 1) / (kFF64Threads * kFF64Targets), p.chunks);
-    if (p.row2)
+    if (p.row2 && skip_self)
+      k_farfield64<true, true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk,
+                                                             kappa, eps, 1.0 / eps, part, ldp);
+    else if (p.row2)
       k_farfield64<true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk,
                                                        kappa, eps, 1.0 / eps, part, ldp);
     else

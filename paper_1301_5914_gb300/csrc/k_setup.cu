@@ -454,9 +454,31 @@ __global__ void k_points(int np, const double* P, int stride, const double* cent
   o[4] = 0.0; o[5] = 0.0; o[6] = 0.0; o[7] = 0.0;
 }
 
+// LOBI-PB (Sec. 2.4): per flat face its centroid, unit normal and area (weight (A, 0, 0)).
+__global__ void k_lobi_geometry(int nf, const int* F, const double* V, double* ny, double* nnu, double* nW,
+                                int* flags) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nf) return;
+  double3 a = ld3(V + 3 * F[3 * j]), b = ld3(V + 3 * F[3 * j + 1]), c = ld3(V + 3 * F[3 * j + 2]);
+  double3 cr = cross(b - a, c - a);
+  double len = sqrt(dot(cr, cr));
+  if (!(len > 0.0) || !isfinite(len)) atomicOr(flags, kDegenerateElement);
+  st3(ny + 3 * (size_t)j, (1.0 / 3.0) * (a + b + c));
+  st3(nnu + 3 * (size_t)j, (1.0 / len) * cr);
+  nW[3 * (size_t)j] = 0.5 * len;
+  nW[3 * (size_t)j + 1] = 0.0;
+  nW[3 * (size_t)j + 2] = 0.0;
+}
+
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_lobi_geometry(int nf, const int* F, const double* V, double* ny, double* nnu, double* nW,
+                                 int* flags, cudaStream_t s) {
+  k_lobi_geometry<<<nblk(nf, 128), 128, 0, s>>>(nf, F, V, ny, nnu, nW, flags);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_adjacency(int nv, int nf, const int* F, int* deg, int* inc_ptr, int* inc_face,
                              int* entry_vertex, cudaStream_t s) {

@@ -28,6 +28,8 @@ HOBI_ERR_BREAKDOWN = -6
 HOBI_ERR_STATE = -7
 HOBI_FP64 = 0
 HOBI_FP32_BULK = 1
+HOBI_SCHEME_HOBI = 0
+HOBI_SCHEME_LOBI = 1
 KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
 
 EXPORTS = [
@@ -49,7 +51,7 @@ class HobiError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mem_device", C.c_int32), ("stream", C.c_void_p),
-                ("restart", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32)]
+                ("restart", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32), ("scheme", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -76,7 +78,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_setup.argtypes = [dp, i64, dp, i64, dp, dp, i64, C.c_double, C.c_double, C.c_double,
                                C.POINTER(Options), C.POINTER(C.c_void_p)]
     lib.hobi_set_precision.argtypes = [vp, C.c_int32]
-    lib.hobi_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    lib.hobi_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.hobi_matvec.argtypes = [vp, dp, dp]
     lib.hobi_rhs.argtypes = [vp, dp]
     lib.hobi_solve.argtypes = [vp, C.c_double, C.c_int32, dp, dp, C.POINTER(SolveInfo)]
@@ -130,11 +132,13 @@ class Solver:
     """One molecule on one GPU (wraps a hobi_t handle).
 
     V [n_v,3], F [n_f,3] int32, N [n_v,3], charges [n_c,4]: all numpy arrays
-    (host mode) or all CUDA torch tensors (device mode).
+    (host mode) or all CUDA torch tensors (device mode). scheme "hobi" (the paper's method) or
+    "lobi" (its low-order comparison scheme: unknowns at the n_f face centroids).
     """
 
     def __init__(self, V, F, N, charges, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
-                 restart: int = 50, use_graph: bool = True, device: int | None = None, stream=None):
+                 restart: int = 50, use_graph: bool = True, device: int | None = None, stream=None,
+                 scheme: str = "hobi"):
         lib = load_library()
         self._lib = lib
         self.device_mode = _is_cuda_tensor(V)
@@ -143,6 +147,7 @@ class Solver:
         opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
         opt.restart = int(restart)
         opt.use_graph = 1 if use_graph else 0
+        opt.scheme = HOBI_SCHEME_LOBI if scheme == "lobi" else HOBI_SCHEME_HOBI
         if self.device_mode:
             import torch
 
@@ -176,7 +181,10 @@ class Solver:
                               float(kappa), C.byref(opt), C.byref(h)))
         self._h = h
         self.nv, self.nf, self.nc = int(nv), int(nf), int(nc)
-        self.n_nodes = 4 * self.nf
+        n_nodes, npts = C.c_int64(), C.c_int64()
+        _check(lib.hobi_sizes(h, None, None, None, C.byref(n_nodes), C.byref(npts)))
+        self.n_nodes, self.npts = int(n_nodes.value), int(npts.value)  # npts: collocation points
+        self.scheme = scheme
         self.eps1, self.eps2, self.kappa = float(eps1), float(eps2), float(kappa)
 
     # ------------------------------------------------------------ helpers
@@ -220,20 +228,20 @@ class Solver:
         _check(self._lib.hobi_set_precision(self._h, HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64))
 
     def matvec(self, u):
-        u = self._in(u, 2 * self.nv)
-        out = self._out(2 * self.nv)
+        u = self._in(u, 2 * self.npts)
+        out = self._out(2 * self.npts)
         _check(self._lib.hobi_matvec(self._h, self._ptr(u), self._ptr(out)))
         return out
 
     def rhs(self):
-        out = self._out(2 * self.nv)
+        out = self._out(2 * self.npts)
         _check(self._lib.hobi_rhs(self._h, self._ptr(out)))
         return out
 
     def solve(self, tol: float = 1e-6, max_it: int = 200, history: int = 0, raise_on_fail: bool = True):
         """Returns (phi, dphi, info dict). info['status'] holds the return code."""
-        phi = self._out(self.nv)
-        dphi = self._out(self.nv)
+        phi = self._out(self.npts)
+        dphi = self._out(self.npts)
         info = SolveInfo()
         hist = None
         if history > 0:
@@ -251,11 +259,11 @@ class Solver:
         return phi, dphi, d
 
     def set_solution(self, u):
-        u = self._in(u, 2 * self.nv)
+        u = self._in(u, 2 * self.npts)
         _check(self._lib.hobi_set_solution(self._h, self._ptr(u)))
 
     def solution(self):
-        out = self._out(2 * self.nv)
+        out = self._out(2 * self.npts)
         _check(self._lib.hobi_get_solution(self._h, self._ptr(out)))
         return out
 
@@ -272,10 +280,11 @@ class Solver:
         return float(e.value)
 
     def nodes(self):
-        """(y, nu, W), each [n_f, 4, 3] FP64."""
+        """(y, nu, W): [n_f, 4, 3] each for HOBI; [n_f, 3] for LOBI (centroid, normal, (area, 0, 0))."""
         outs = [self._out(3 * self.n_nodes) for _ in range(3)]
         _check(self._lib.hobi_get_nodes(self._h, *[self._ptr(o) for o in outs]))
-        return tuple(o.reshape(self.nf, 4, 3) for o in outs)
+        shape = (self.nf, 4, 3) if self.scheme != "lobi" else (self.nf, 3)
+        return tuple(o.reshape(shape) for o in outs)
 
     def correction(self):
         """(vertex[e], face[e], coeff[e,3,4]) for every (vertex, incident face) entry."""
