@@ -82,6 +82,13 @@ typedef struct {
   int32_t use_graph;  /* 1 (default): replay each GMRES iteration as a captured CUDA graph */
   int32_t device;     /* CUDA device ordinal; -1 (default): the current device */
   int32_t scheme;     /* hobi_scheme (default HOBI_SCHEME_HOBI); the batch API accepts HOBI only */
+  int32_t autotune;   /* 1 (default): hobi_setup times the candidate FP32 far-field block shapes
+                         (threads x targets per thread x source-tile size) on the problem and keeps
+                         the fastest; decisions are cached per process by problem size, and in the
+                         file named by the environment variable HOBI_AUTOTUNE_CACHE if set.
+                         0: the analytic planner's choice. */
+  int32_t ff_shape;   /* -1 (default): chosen as above; 0..3: use that FP32 block shape (see
+                         hobi_plan_info) */
 } hobi_options;
 
 typedef struct {
@@ -195,6 +202,11 @@ int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* 
 /* Number of CUDA kernels this handle has launched since hobi_setup began (setup included;
  * a replayed GMRES graph counts each of its kernels). */
 int hobi_kernel_launches(hobi_t h, int64_t* n);
+
+/* The FP32 far-field launch plan of the matvec: block shape index (0: 256 threads x 4 targets,
+ * 256-node tiles; 1: 128 x 4, 128; 2: 128 x 2, 64; 3: 64 x 2, 64), source chunks, and whether
+ * the shape was measured by the autotuner (1) or chosen analytically (0). */
+int hobi_plan_info(hobi_t h, int32_t* shape, int32_t* chunks, int32_t* tuned);
 
 /* Free every resource of the handle (NULL is a no-op). */
 void hobi_destroy(hobi_t h);

@@ -29,15 +29,15 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 
 __device__ __forceinline__ float2 pair_of(float a) { return make_float2(a, a); }
 
-// One block's share of the FP32 far field: targets bx*1024 .. bx*1024+1023 (4 per thread)
-// against source tiles [t0, t1); results (FP64) to out[i] (row 1) and out[nt + i] (row 2).
-// sh: 4 kTile float4 of shared memory. SKIP_SELF: a pair at zero distance (a collocation point
-// that is also a source node, LOBI-PB) contributes nothing.
-template <bool ROW2, bool SKIP_SELF = false>
+// One block's share of the FP32 far field: NT threads, 2 TP targets per thread (targets
+// bx*NT*2TP ...), against source tiles [t0, t1) of TILE nodes; results (FP64) to out[i] (row 1)
+// and out[nt + i] (row 2). sh: 4 TILE float4 of shared memory. SKIP_SELF: a pair at zero
+// distance (a collocation point that is also a source node, LOBI-PB) contributes nothing.
+template <bool ROW2, bool SKIP_SELF = false, int NT = kFF32Threads, int TP = kFF32Targets / 2, int TILE = kTile>
 __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src,
                                            int t0, int t1, float neg_kl2e, float kap, float eps,
                                            double* __restrict__ out, int bx, float4* sh) {
-  constexpr int T = kFF32Targets, TP = kFF32Targets / 2, NT = kFF32Threads;
+  constexpr int T = 2 * TP;
   float2 px[TP], py[TP], pz[TP];  // target k = 2p + lane
   float qx[T], qy[T], qz[T];
   float h1[T], l1[T], h2[T], l2[T];
@@ -58,14 +58,14 @@ __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int n
   const float2 m1 = pair_of(-1.f), three = pair_of(3.f), m3 = pair_of(-3.f);
   for (int tile = t0; tile < t1; ++tile) {
     __syncthreads();
-    const float4* g = src + (size_t)tile * (4 * kTile);
-    for (int q = threadIdx.x; q < 4 * kTile; q += NT) sh[q] = g[q];
+    const float4* g = src + (size_t)tile * (4 * TILE);
+    for (int q = threadIdx.x; q < 4 * TILE; q += NT) sh[q] = g[q];
     __syncthreads();
     float2 a1[TP], wx[TP], wy[TP], wz[TP];
 #pragma unroll
     for (int k = 0; k < TP; ++k) a1[k] = wx[k] = wy[k] = wz[k] = pair_of(0.f);
 #pragma unroll 2
-    for (int s = 0; s < kTile; ++s) {
+    for (int s = 0; s < TILE; ++s) {
       const float4 A = sh[4 * s], B = sh[4 * s + 1], C = sh[4 * s + 2], D = sh[4 * s + 3];
       const float2 nyx = make_float2(A.x, A.y), nyy = make_float2(A.z, A.w), nyz = make_float2(B.x, B.y);
       const float2 sg = make_float2(B.z, B.w), mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w);

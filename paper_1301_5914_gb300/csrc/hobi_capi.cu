@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <mutex>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string>
 #include <vector>
 
@@ -35,6 +37,8 @@ int fail(int code, const std::string& msg) {
     if (r_ != HOBI_OK) return r_; \
   } while (0)
 
+int choose_shape(int n_targets, int n_pad, int num_sms);
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -56,6 +60,7 @@ struct hobi_ctx {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   int mem_device = 0, precision = HOBI_FP32_BULK, restart = 50, use_graph = 1, scheme = HOBI_SCHEME_HOBI;
+  int autotune = 1, tuned = 0, ff_shape = -1;
   // nv: collocation points (mesh vertices for HOBI, face centroids for LOBI); nv_mesh: mesh vertices
   int64_t nv = 0, nf = 0, nc = 0, n_nodes = 0, n_pad = 0, nv_mesh = 0;
   int* zero_ptr = nullptr;  // LOBI: an all-zero incidence row pointer (no singular correction)
@@ -319,7 +324,8 @@ struct hobi_ctx {
   // phi_reac at np targets already in (t32, t64), row 1 only, from the current solution x
   int reaction_dev(int64_t np, const float4* t32, const double* t64, double* phi) {
     const bool fp32 = precision == HOBI_FP32_BULK;
-    FarFieldPlan p = plan_farfield(fp32, (int)np, (int)n_pad, false, num_sms, farfield_blocks_per_sm(fp32, false));
+    const int sh = fp32 ? choose_shape((int)np, (int)n_pad, num_sms) : 0;
+    FarFieldPlan p = plan_farfield(fp32, (int)np, (int)n_pad, false, num_sms, farfield_blocks_per_sm(fp32, false, sh), sh);
     HOBI_TRY(ensure_ppart((size_t)p.chunks * (size_t)np));
     HOBI_TRY(gather(fp32, x, nullptr, 0));
     HOBI_TRY(farfield(fp32, p, t32, t64, ppart));
@@ -353,6 +359,66 @@ struct hobi_ctx {
 };
 
 namespace {
+
+// Analytic shape choice: the largest block shape that still yields enough independent
+// (target block, source tile) work items to fill the machine several times over.
+int choose_shape(int n_targets, int n_pad, int num_sms) {
+  static const int per_block[kNumFF32Shapes] = {1024, 512, 256, 128};
+  static const int tile[kNumFF32Shapes] = {256, 128, 64, 64};
+  for (int s = 0; s < kNumFF32Shapes; ++s) {
+    long tt = (n_targets + per_block[s] - 1) / per_block[s];
+    long tiles = n_pad / tile[s];
+    if (tt * std::min<long>(tiles, 512) >= 8L * num_sms * farfield_blocks_per_sm(true, true, s)) return s;
+  }
+  return kNumFF32Shapes - 1;
+}
+
+// Autotuner decisions, per process (and optionally in a file): key -> shape
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, int>> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(int device, int scheme, int64_t nv, int64_t n_pad) {
+  cudaDeviceProp prop;
+  std::string name = cudaGetDeviceProperties(&prop, device) == cudaSuccess ? prop.name : "gpu";
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  return name + " " + std::to_string(scheme) + " " + std::to_string(nv) + " " + std::to_string(n_pad);
+}
+
+bool tune_lookup(const std::string& key, int* shape) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (!g_tune_loaded) {
+    g_tune_loaded = true;
+    if (const char* path = getenv("HOBI_AUTOTUNE_CACHE")) {
+      if (FILE* f = fopen(path, "r")) {
+        char a[256], b[32], c[32], d[32];
+        int sh;
+        while (fscanf(f, "%255s %31s %31s %31s %d", a, b, c, d, &sh) == 5)
+          if (sh >= 0 && sh < kNumFF32Shapes)
+            g_tune.emplace_back(std::string(a) + " " + b + " " + c + " " + d, sh);
+        fclose(f);
+      }
+    }
+  }
+  for (auto& kv : g_tune)
+    if (kv.first == key) {
+      *shape = kv.second;
+      return true;
+    }
+  return false;
+}
+
+void tune_store(const std::string& key, int shape) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.emplace_back(key, shape);
+  if (const char* path = getenv("HOBI_AUTOTUNE_CACHE")) {
+    if (FILE* f = fopen(path, "a")) {
+      fprintf(f, "%s %d\n", key.c_str(), shape);
+      fclose(f);
+    }
+  }
+}
 
 std::string mesh_message(int fl) {
   std::string m = "invalid mesh:";
@@ -465,14 +531,53 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
     HOBI_CK(cudaStreamSynchronize(h->stream));
     return HOBI_OK;
   }
-  // far-field plans and partial-sum buffers
+  // far-field plans and partial-sum buffers (room for every FP32 shape the autotuner may try)
+  const bool skip = h->scheme == HOBI_SCHEME_LOBI;
+  FarFieldPlan cand[kNumFF32Shapes];
   size_t part_elems = 0;
-  for (int fp32 = 0; fp32 < 2; ++fp32) {
-    h->plan[fp32] = plan_farfield(fp32, (int)h->nv, (int)h->n_pad, true, h->num_sms, farfield_blocks_per_sm(fp32, true));
-    size_t need = (size_t)h->plan[fp32].chunks * 2 * h->nv;
-    if (need > part_elems) part_elems = need;
+  for (int sh = 0; sh < kNumFF32Shapes; ++sh) {
+    cand[sh] = plan_farfield(true, (int)h->nv, (int)h->n_pad, true, h->num_sms, farfield_blocks_per_sm(true, true, sh),
+                             sh);
+    part_elems = std::max(part_elems, (size_t)cand[sh].chunks * 2 * h->nv);
   }
+  h->plan[0] = plan_farfield(false, (int)h->nv, (int)h->n_pad, true, h->num_sms, farfield_blocks_per_sm(false, true));
+  part_elems = std::max(part_elems, (size_t)h->plan[0].chunks * 2 * h->nv);
   HOBI_TRY(h->alloc(&h->part, part_elems));
+  int shape = choose_shape((int)h->nv, (int)h->n_pad, h->num_sms);
+  if (h->ff_shape >= 0) {
+    shape = h->ff_shape;
+  } else if (h->autotune) {
+    const std::string key = tune_key(h->device, h->scheme, h->nv, h->n_pad);
+    if (tune_lookup(key, &shape)) {
+      h->tuned = 1;
+    } else {
+      // time every shape on this problem (densities of u = 0; the timing does not depend on them)
+      HOBI_CK(cudaMemsetAsync(h->x, 0, sizeof(double) * 2 * h->nv, h->stream));
+      HOBI_TRY(h->gather(true, h->x, nullptr, 0));
+      float best = 1e30f;
+      for (int sh = 0; sh < kNumFF32Shapes; ++sh) {
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          HOBI_CK(cudaEventRecord(h->ev_t0, h->stream));
+          HOBI_CK(launch_farfield(true, cand[sh], h->tgt32, h->tgt64, h->src32, h->src64, h->eps, h->kappa, h->part,
+                                  h->stream, skip));
+          HOBI_CK(cudaEventRecord(h->ev_t1, h->stream));
+          HOBI_CK(cudaEventSynchronize(h->ev_t1));
+          float ms = 0.f;
+          HOBI_CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+          if (rep > 0) t = std::min(t, ms);  // the first launch warms up
+        }
+        h->launches += 3;
+        if (t < best * 0.98f) {  // prefer the earlier (larger) shape unless clearly faster
+          best = t;
+          shape = sh;
+        }
+      }
+      tune_store(key, shape);
+      h->tuned = 1;
+    }
+  }
+  h->plan[1] = cand[shape];
 
   // iterate vectors and GMRES workspace
   const int64_t n = 2 * h->nv;
@@ -512,6 +617,8 @@ void hobi_default_options(hobi_options* opt) {
   opt->use_graph = 1;
   opt->device = -1;
   opt->scheme = HOBI_SCHEME_HOBI;
+  opt->autotune = 1;
+  opt->ff_shape = -1;
 }
 
 const char* hobi_last_error(void) { return g_err.c_str(); }
@@ -540,6 +647,7 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   if (opt) o = *opt;
   if (o.precision != HOBI_FP64 && o.precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
   if (o.scheme != HOBI_SCHEME_HOBI && o.scheme != HOBI_SCHEME_LOBI) return fail(HOBI_ERR_ARG, "unknown scheme");
+  if (o.ff_shape < -1 || o.ff_shape >= kNumFF32Shapes) return fail(HOBI_ERR_ARG, "ff_shape must be -1 or 0..3");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
 
@@ -557,6 +665,8 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   h->restart = o.restart;
   h->use_graph = o.use_graph ? 1 : 0;
   h->scheme = o.scheme;
+  h->autotune = o.autotune ? 1 : 0;
+  h->ff_shape = o.ff_shape;
   h->nv = n_v;
   h->nf = n_f;
   h->nc = n_c;
@@ -820,6 +930,14 @@ int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* 
   h->prof_ms = 0.0;
   h->prof_launches = 0;
   h->prof_pairs = 0.0;
+  return HOBI_OK;
+}
+
+int hobi_plan_info(hobi_t h, int32_t* shape, int32_t* chunks, int32_t* tuned) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (shape) *shape = h->plan[1].shape;
+  if (chunks) *chunks = h->plan[1].chunks;
+  if (tuned) *tuned = h->tuned;
   return HOBI_OK;
 }
 

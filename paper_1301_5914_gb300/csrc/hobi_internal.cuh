@@ -82,16 +82,20 @@ cudaError_t launch_gather(bool fp32, int n_nodes, int n_pad, int nv, const int* 
                           cudaStream_t s);
 cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* src64, cudaStream_t s);
 
+// FP32 far-field block shapes (threads, targets per thread, source tile): 0 = 256 x 4, tile 256;
+// 1 = 128 x 4, tile 128; 2 = 128 x 2, tile 64; 3 = 64 x 2, tile 64 (small problems).
+constexpr int kNumFF32Shapes = 4;
 struct FarFieldPlan {
   int n_targets;
-  int n_tiles;          // source tiles of kTile nodes
+  int n_tiles;          // source tiles (of the shape's tile size; kTile for FP64)
   int tiles_per_chunk;
   int chunks;
   bool row2;            // compute the second row (K3, K4) too
+  int shape;            // FP32 block shape
 };
 FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2, int num_sms,
-                           int blocks_per_sm);
-int farfield_blocks_per_sm(bool fp32, bool row2);
+                           int blocks_per_sm, int shape = 0);
+int farfield_blocks_per_sm(bool fp32, bool row2, int shape = 0);
 // skip_self: pairs at zero distance contribute nothing (LOBI-PB, where targets are source nodes)
 cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt32, const double* tgt64,
                             const float4* src32, const double* src64, double eps, double kappa,

@@ -76,13 +76,13 @@ __global__ void k_pad(int n_nodes, int n_pad, float4* src32, double* src64) {
 }
 
 // ------------------------------------------------------------------ far field kernels
-template <bool ROW2, bool SKIP_SELF = false>
-__global__ void __launch_bounds__(kFF32Threads, 2)
+template <bool ROW2, bool SKIP_SELF, int NT, int TP, int TILE>
+__global__ void __launch_bounds__(NT, 512 / NT)
     k_farfield32(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src, int n_tiles, int tpc,
                  float neg_kl2e, float kap, float eps, double* __restrict__ part, int64_t ldp) {
-  __shared__ float4 sh[4 * kTile];
+  __shared__ float4 sh[4 * TILE];
   const int t0 = blockIdx.y * tpc;
-  ff::ff32_block<ROW2, SKIP_SELF>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), neg_kl2e, kap, eps,
+  ff::ff32_block<ROW2, SKIP_SELF, NT, TP, TILE>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), neg_kl2e, kap, eps,
                        part + (size_t)blockIdx.y * ldp, blockIdx.x, sh);
 }
 
@@ -158,30 +158,72 @@ cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* sr
   return cudaGetLastError();
 }
 
-int farfield_blocks_per_sm(bool fp32, bool row2) {
+// FP32 block shapes the planner and the autotuner choose from: threads, target pairs per thread,
+// source nodes per shared-memory tile. Shape 0 is the default for large problems.
+struct FF32Shape {
+  int nt, tp, tile;
+};
+constexpr FF32Shape kShapes[kNumFF32Shapes] = {{256, 2, 256}, {128, 2, 128}, {128, 1, 64}, {64, 1, 64}};
+
+template <bool ROW2, bool SKIP>
+cudaError_t launch32_shape(int shape, dim3 grid, const float4* tgt, int nt, const float4* src, int n_tiles, int tpc,
+                           float nk, float kap, float eps, double* part, int64_t ldp, cudaStream_t s) {
+  switch (shape) {
+    case 1:
+      k_farfield32<ROW2, SKIP, 128, 2, 128><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+      break;
+    case 2:
+      k_farfield32<ROW2, SKIP, 128, 1, 64><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+      break;
+    case 3:
+      k_farfield32<ROW2, SKIP, 64, 1, 64><<<grid, 64, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+      break;
+    default:
+      k_farfield32<ROW2, SKIP, 256, 2, 256><<<grid, 256, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+  }
+  return cudaGetLastError();
+}
+
+template <bool ROW2, bool SKIP>
+int occupancy32(int shape) {
   int n = 1;
-  if (fp32) {
-    if (row2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<true>, kFF32Threads, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<false>, kFF32Threads, 0);
-  } else {
-    if (row2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<true>, kFF64Threads, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<false>, kFF64Threads, 0);
+  switch (shape) {
+    case 1:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 128, 2, 128>, 128, 0);
+      break;
+    case 2:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 128, 1, 64>, 128, 0);
+      break;
+    case 3:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 64, 1, 64>, 64, 0);
+      break;
+    default:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 256, 2, 256>, 256, 0);
   }
   return n > 0 ? n : 1;
 }
 
-// Choose the number of source chunks so that (target tiles x chunks) equal-sized blocks fill the
-// machine's block slots with the least idle time in the last wave.
-FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2, int num_sms, int blocks_per_sm) {
+int farfield_blocks_per_sm(bool fp32, bool row2, int shape) {
+  int n = 1;
+  if (fp32) return row2 ? occupancy32<true, false>(shape) : occupancy32<false, false>(shape);
+  if (row2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<true>, kFF64Threads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<false>, kFF64Threads, 0);
+  return n > 0 ? n : 1;
+}
+
+// Number of source chunks for a shape: (target blocks x chunks) equal-sized blocks filling the
+// machine's block slots with the least idle time in the last wave. Tiles are `tile` nodes.
+FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2, int num_sms, int blocks_per_sm,
+                           int shape) {
   FarFieldPlan p;
   p.n_targets = n_targets;
   p.row2 = row2;
-  p.n_tiles = n_nodes_pad / kTile;
-  const int per_block = fp32 ? kFF32Threads * kFF32Targets : kFF64Threads * kFF64Targets;
+  p.shape = fp32 ? shape : 0;
+  const int tile = fp32 ? kShapes[p.shape].tile : kTile;
+  p.n_tiles = n_nodes_pad / tile;
+  const int per_block = fp32 ? kShapes[p.shape].nt * 2 * kShapes[p.shape].tp : kFF64Threads * kFF64Targets;
   const int tt = (n_targets + per_block - 1) / per_block;
   const long slots = (long)num_sms * blocks_per_sm;
   const int cmax = p.n_tiles < 512 ? p.n_tiles : 512;
@@ -209,29 +251,29 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
                             cudaStream_t s, bool skip_self) {
   const int64_t ldp = p.row2 ? 2 * (int64_t)p.n_targets : (int64_t)p.n_targets;
   if (fp32) {
-    dim3 grid((p.n_targets + kFF32Threads * kFF32Targets - 1) / (kFF32Threads * kFF32Targets), p.chunks);
-    const float neg_kl2e = (float)(-kappa * 1.4426950408889634074);
+    const FF32Shape& sh = kShapes[p.shape];
+    const int per_block = sh.nt * 2 * sh.tp;
+    dim3 grid((p.n_targets + per_block - 1) / per_block, p.chunks);
+    const float nk = (float)(-kappa * 1.4426950408889634074);
     if (p.row2 && skip_self)
-      k_farfield32<true, true><<<grid, kFF32Threads, 0, s>>>(tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk,
-                                                             neg_kl2e, (float)kappa, (float)eps, part, ldp);
-    else if (p.row2)
-      k_farfield32<true><<<grid, kFF32Threads, 0, s>>>(tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk,
-                                                       neg_kl2e, (float)kappa, (float)eps, part, ldp);
-    else
-      k_farfield32<false><<<grid, kFF32Threads, 0, s>>>(tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk,
-                                                        neg_kl2e, (float)kappa, (float)eps, part, ldp);
-  } else {
-    dim3 grid((p.n_targets + kFF64Threads * kFF64Targets - 1) / (kFF64Threads * kFF64Targets), p.chunks);
-    if (p.row2 && skip_self)
-      k_farfield64<true, true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk,
-                                                             kappa, eps, 1.0 / eps, part, ldp);
-    else if (p.row2)
-      k_farfield64<true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk,
-                                                       kappa, eps, 1.0 / eps, part, ldp);
-    else
-      k_farfield64<false><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk,
-                                                        kappa, eps, 1.0 / eps, part, ldp);
+      return launch32_shape<true, true>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
+                                        (float)kappa, (float)eps, part, ldp, s);
+    if (p.row2)
+      return launch32_shape<true, false>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
+                                         (float)kappa, (float)eps, part, ldp, s);
+    return launch32_shape<false, false>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
+                                        (float)kappa, (float)eps, part, ldp, s);
   }
+  dim3 grid((p.n_targets + kFF64Threads * kFF64Targets - 1) / (kFF64Threads * kFF64Targets), p.chunks);
+  if (p.row2 && skip_self)
+    k_farfield64<true, true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk,
+                                                           kappa, eps, 1.0 / eps, part, ldp);
+  else if (p.row2)
+    k_farfield64<true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk, kappa,
+                                                     eps, 1.0 / eps, part, ldp);
+  else
+    k_farfield64<false><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk, kappa,
+                                                      eps, 1.0 / eps, part, ldp);
   return cudaGetLastError();
 }
 

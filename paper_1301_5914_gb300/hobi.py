@@ -36,7 +36,7 @@ EXPORTS = [
     "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
     "hobi_solve", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
     "hobi_reaction_potential_noalloc", "hobi_energy",
-    "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches",
+    "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
     "hobi_matvec_batch", "hobi_solve_batch", "hobi_energy_batch", "hobi_batch_kernel_launches", "hobi_destroy_batch",
     "hobi_batch_profile_enable", "hobi_batch_profile_read",
@@ -51,7 +51,8 @@ class HobiError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mem_device", C.c_int32), ("stream", C.c_void_p),
-                ("restart", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32), ("scheme", C.c_int32)]
+                ("restart", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32), ("scheme", C.c_int32),
+                ("autotune", C.c_int32), ("ff_shape", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_profile_enable.argtypes = [vp, C.c_int32]
     lib.hobi_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(C.c_double)]
     lib.hobi_kernel_launches.argtypes = [vp, C.POINTER(i64)]
+    lib.hobi_plan_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.hobi_destroy.argtypes = [vp]
     lib.hobi_destroy.restype = None
     lib.hobi_setup_batch.argtypes = [C.c_int32, dp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
@@ -138,7 +140,7 @@ class Solver:
 
     def __init__(self, V, F, N, charges, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
                  restart: int = 50, use_graph: bool = True, device: int | None = None, stream=None,
-                 scheme: str = "hobi"):
+                 scheme: str = "hobi", autotune: bool = True, ff_shape: int = -1):
         lib = load_library()
         self._lib = lib
         self.device_mode = _is_cuda_tensor(V)
@@ -148,6 +150,8 @@ class Solver:
         opt.restart = int(restart)
         opt.use_graph = 1 if use_graph else 0
         opt.scheme = HOBI_SCHEME_LOBI if scheme == "lobi" else HOBI_SCHEME_HOBI
+        opt.autotune = 1 if autotune else 0
+        opt.ff_shape = int(ff_shape)
         if self.device_mode:
             import torch
 
@@ -301,6 +305,12 @@ class Solver:
         n = C.c_int64()
         _check(self._lib.hobi_kernel_launches(self._h, C.byref(n)))
         return int(n.value)
+
+    def plan_info(self):
+        """FP32 far-field plan: {'shape', 'chunks', 'tuned'}."""
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._lib.hobi_plan_info(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"shape": a.value, "chunks": b.value, "tuned": bool(c.value)}
 
     def profile_enable(self, on: bool = True):
         _check(self._lib.hobi_profile_enable(self._h, 1 if on else 0))

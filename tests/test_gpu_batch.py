@@ -36,11 +36,11 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-8)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
 def test_batch_matches_single_solves(molecules, prec, tol):
-    """FP64: same arithmetic up to the order of FP64 chunk sums. FP32: the batch groups the
-    compensated tile sums in 16-tile tasks, the single plan in its own chunks -- a change far
-    below the FP32-bulk tolerance (1e-4)."""
+    """FP64: same arithmetic up to the order of FP64 chunk sums. FP32: the batch uses the
+    256-node tile shape in 16-tile tasks while a single solve may use another autotuned shape
+    (other FP32 tile sums) -- differences far below the FP32-bulk tolerance (1e-4)."""
     bs = hobi.BatchSolver(molecules, EPS1, EPS2, KAPPA, precision=prec)
     phis, dphis, info = bs.solve(1e-6, 200)
     assert info["converged"] and np.all(info["mol_status"] == 0)

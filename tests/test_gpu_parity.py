@@ -303,3 +303,29 @@ def test_profiling_counts_farfield_launches_with_graphs(problems):
     assert prof["farfield_ms"] > 0
     assert prof["pairs"] == (prof["launches"] - 1) * b.nv * b.n_nodes + b.nc * b.n_nodes
     assert b.kernel_launches() > 14 * ib["iterations"]
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", ["hobi", "lobi"])
+def test_every_block_shape_matches_oracle(problems, shape, scheme):
+    """Each FP32 far-field block shape the autotuner may pick gives the same operator."""
+    V, F, N, Q, e1, e2, ka, orc = problems["c2_l4"]
+    s = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp32", scheme=scheme, ff_shape=shape)
+    assert s.plan_info()["shape"] == shape
+    ref_p = orc if scheme == "hobi" else oracle.LobiProblem(V, F, N, Q, e1, e2, ka)
+    u = np.random.default_rng(8).normal(size=2 * s.npts)
+    assert _rel(s.matvec(u), ref_p.matvec(u)) <= 1e-5
+    u_ref, it_ref, _, _ = ref_p.gmres(1e-6)
+    phi, dphi, info = s.solve(1e-6)
+    assert abs(info["iterations"] - it_ref) <= 1
+    assert _rel(np.concatenate([phi, dphi]), u_ref) <= 1e-4
+
+
+def test_autotuner_decides_once_per_size(problems):
+    V, F, N, Q, e1, e2, ka, _ = problems["c1_l3"]
+    a = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp32")
+    b = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp32")
+    ia, ib = a.plan_info(), b.plan_info()
+    assert ia["tuned"] and ib["tuned"] and ia["shape"] == ib["shape"]
+    c = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp32", autotune=False)
+    assert not c.plan_info()["tuned"]
