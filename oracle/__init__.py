@@ -14,7 +14,6 @@ from __future__ import annotations
 import ctypes as C
 import os
 import subprocess
-import sys
 
 import numpy as np
 

@@ -49,12 +49,13 @@ enum MeshFlag : int {
 // builds inc_ptr/inc_face (rows sorted by face) and entry_vertex[3 nf] (entry -> vertex)
 cudaError_t launch_adjacency(int nv, int nf, const int* F, int* deg, int* inc_ptr, int* inc_face,
                              int* entry_vertex, cudaStream_t s);
+// validation runs kValidateBlocks blocks; vol_part[kValidateBlocks], center_part[3 kValidateBlocks]
+constexpr int kValidateBlocks = 256;
 cudaError_t launch_validate(int nv, int nf, int nc, const double* V, const double* Nv_in, const int* F,
                             const int* inc_ptr, const int* inc_face, const double* Q, double* Nv_unit,
-                            double* vol_part, int vol_blocks, double* center_part, int* flags,
-                            cudaStream_t s);
-cudaError_t launch_finish_validate(int nv, const double* vol_part, int vol_blocks, const double* center_part,
-                                   double* center, int* flags, cudaStream_t s);
+                            double* vol_part, double* center_part, int* flags, cudaStream_t s);
+cudaError_t launch_finish_validate(int nv, const double* vol_part, const double* center_part, double* center,
+                                   int* flags, cudaStream_t s);
 // sets kDegenerateElement in *flags if a quadrature node's Jacobian is zero or not finite
 cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double* Nv, double* elem, double* ny,
                             double* nnu, double* nW, int* flags, cudaStream_t s);
@@ -76,7 +77,7 @@ cudaError_t launch_points(int np, const double* P, int stride, const double* cen
 // ---- far field (k_farfield.cu) ----
 // Source densities of the current iterate u (2 n_v) for every node; padded nodes stay inert.
 // If kptr != nullptr the vector is u + (*kptr) * ld (GMRES basis column).
-cudaError_t launch_gather(bool fp32, int n_nodes, int n_pad, int nv, const int* F, const double* ny,
+cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
                           const int* kptr, int64_t ld, double inv_eps, float4* src32, double* src64,
                           cudaStream_t s);
@@ -159,6 +160,7 @@ struct MolDesc {          // one molecule's device tables (owned by its single-m
 };
 struct FFTask {           // one persistent far-field work item
   int mol, bx, t0, t1, chunk;
+  int narrow;             // FP32: 1 = 2 targets per thread (512 per block), 0 = 4 (1024 per block)
 };
 struct Segment {          // piece of the concatenated vector inside one molecule
   int64_t start;

@@ -82,8 +82,12 @@ __global__ void __launch_bounds__(kFF32Threads, 2)
     const FFTask tk = tasks[t];
     if (mol_done(ms, tk.mol)) continue;
     const MolDesc& d = mols[tk.mol];
-    ff::ff32_block<true>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap, eps,
-                         d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh);
+    if (tk.narrow)  // small molecules: 512 targets per block wastes fewer idle lanes
+      ff::ff32_block<true, false, kFF32Threads, 1, kTile>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap, eps,
+                                                          d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh);
+    else
+      ff::ff32_block<true>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap, eps,
+                           d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh);
   }
 }
 

@@ -134,11 +134,10 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_gather(bool fp32, int n_nodes, int n_pad, int nv, const int* F, const double* ny,
+cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
                           const int* kptr, int64_t ld, double inv_eps, float4* src32, double* src64,
                           cudaStream_t s) {
-  (void)n_pad;
   if (fp32)
     k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, src32);
   else

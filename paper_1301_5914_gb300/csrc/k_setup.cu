@@ -106,7 +106,6 @@ __device__ __forceinline__ bool has_directed_edge(const int* f, int p, int q) {
   return (f[0] == p && f[1] == q) || (f[1] == p && f[2] == q) || (f[2] == p && f[0] == q);
 }
 
-constexpr int kValBlocks = 256;
 constexpr int kValThreads = 256;
 
 __global__ void k_validate_faces(int nv, int nf, const double* V, const int* F, const int* ptr,
@@ -495,17 +494,16 @@ cudaError_t launch_adjacency(int nv, int nf, const int* F, int* deg, int* inc_pt
 
 cudaError_t launch_validate(int nv, int nf, int nc, const double* V, const double* Nv_in, const int* F,
                             const int* inc_ptr, const int* inc_face, const double* Q, double* Nv_unit,
-                            double* vol_part, int vol_blocks, double* center_part, int* flags, cudaStream_t s) {
-  (void)vol_blocks;
-  k_validate_faces<<<kValBlocks, kValThreads, 0, s>>>(nv, nf, V, F, inc_ptr, inc_face, vol_part, flags);
-  k_validate_vertices<<<kValBlocks, kValThreads, 0, s>>>(nv, V, Nv_in, inc_ptr, Nv_unit, center_part, flags);
+                            double* vol_part, double* center_part, int* flags, cudaStream_t s) {
+  k_validate_faces<<<kValidateBlocks, kValThreads, 0, s>>>(nv, nf, V, F, inc_ptr, inc_face, vol_part, flags);
+  k_validate_vertices<<<kValidateBlocks, kValThreads, 0, s>>>(nv, V, Nv_in, inc_ptr, Nv_unit, center_part, flags);
   if (nc > 0) k_validate_charges<<<nblk(nc, 256), 256, 0, s>>>(nc, Q, flags);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish_validate(int nv, const double* vol_part, int vol_blocks, const double* center_part,
-                                   double* center, int* flags, cudaStream_t s) {
-  k_finish_validate<<<1, 32, 0, s>>>(nv, vol_part, vol_blocks, center_part, center, flags);
+cudaError_t launch_finish_validate(int nv, const double* vol_part, const double* center_part, double* center,
+                                   int* flags, cudaStream_t s) {
+  k_finish_validate<<<1, 32, 0, s>>>(nv, vol_part, kValidateBlocks, center_part, center, flags);
   return cudaGetLastError();
 }
 
