@@ -145,6 +145,14 @@ int hobi_rhs(hobi_t h, double* b);
 int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi,
                hobi_solve_info* info);
 
+/* Warm start / resume: as hobi_solve, but GMRES starts from x0 = u0 (2 n_v doubles) or, when u0
+ * is NULL, from the handle's current solution (a previous solve or hobi_set_solution; else
+ * HOBI_ERR_STATE). The stopping test stays ||b - A u|| / ||b|| <= tol, so resuming a solve that
+ * stopped at a loose tolerance continues it, and a converged u0 returns after 0 iterations. The
+ * paper has no counterpart (its GMRES starts from an unstated guess). */
+int hobi_solve_from(hobi_t h, const double* u0, double tol, int32_t max_it, double* phi, double* dphi,
+                    hobi_solve_info* info);
+
 /* Replace the handle's solution by u (2 n_v doubles), e.g. to evaluate the energy of a given
  * surface potential. */
 int hobi_set_solution(hobi_t h, const double* u);

@@ -754,26 +754,46 @@ int hobi_rhs(hobi_t h, double* b) {
   return h->finish();
 }
 
-int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, hobi_solve_info* info) {
+}  // extern "C"
+
+namespace {
+// GMRES driver. warm: start from x0 (u0, or the handle's current solution when u0 is NULL);
+// the residual test stays relative to ||b||.
+int solve_impl(hobi_t h, const double* u0, bool warm, double tol, int32_t max_it, double* phi, double* dphi,
+               hobi_solve_info* info) {
   if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
   if (!(tol > 0.0) || max_it < 1) return fail(HOBI_ERR_ARG, "need tol > 0 and max_it >= 1");
+  if (warm && !u0 && !h->have_solution)
+    return fail(HOBI_ERR_STATE, "no solution to resume from: pass u0 or solve first");
   DeviceGuard guard(h->device);
   const int64_t n = 2 * h->nv;
   const int m = h->restart;
   HOBI_TRY(h->enter());
   HOBI_CK(cudaEventRecord(h->ev_t0, h->stream));
-  // initial state: x = 0, r = b
+  // ||b|| fixes the relative residual; cold start: x = 0, r = b
   GmresState s0;
   memset(&s0, 0, sizeof s0);
   s0.tol = tol;
   *h->st_host = s0;
   HOBI_CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(GmresState), cudaMemcpyHostToDevice, h->stream));
-  HOBI_CK(cudaMemsetAsync(h->x, 0, sizeof(double) * n, h->stream));
+  if (warm) {
+    if (u0) HOBI_TRY(h->copy_in(h->x, u0, n));
+  } else {
+    HOBI_CK(cudaMemsetAsync(h->x, 0, sizeof(double) * n, h->stream));
+  }
   HOBI_CK(cudaMemcpyAsync(h->Vb, h->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
   HOBI_CK(launch_dots(nullptr, 0, h->Vb, n, h->st, 1, h->dpart, h->stream));
   HOBI_CK(launch_reduce_dots(h->dpart, m, h->st, 1, h->nrm, nullptr, 0, h->stream));
   HOBI_CK(launch_cycle_start(h->Vb, n, h->nrm, h->st, h->g, m, 1, h->stream));
   h->launches += 3;
+  if (warm) {  // r0 = b - A x0 replaces the first basis vector
+    HOBI_TRY(h->matvec_dev(h->x, nullptr, 0, h->w));
+    HOBI_CK(launch_residual_start(h->b, h->w, h->Vb, n, h->stream));
+    HOBI_CK(launch_dots(nullptr, 0, h->Vb, n, h->st, 1, h->dpart, h->stream));
+    HOBI_CK(launch_reduce_dots(h->dpart, m, h->st, 1, h->nrm, nullptr, 0, h->stream));
+    HOBI_CK(launch_cycle_start(h->Vb, n, h->nrm, h->st, h->g, m, 0, h->stream));
+    h->launches += 4;
+  }
   HOBI_TRY(h->read_state());
   std::vector<double> hist;
   hist.push_back(h->st_host->rel);
@@ -824,6 +844,18 @@ int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, 
   if (fs.breakdown) return fail(HOBI_ERR_BREAKDOWN, "GMRES breakdown (zero or non-finite Arnoldi norm)");
   return fail(HOBI_ERR_NOT_CONVERGED, "GMRES did not reach tol within max_it iterations (rel residual " +
                                           std::to_string(fs.rel) + ")");
+}
+}  // namespace
+
+extern "C" {
+
+int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, hobi_solve_info* info) {
+  return solve_impl(h, nullptr, false, tol, max_it, phi, dphi, info);
+}
+
+int hobi_solve_from(hobi_t h, const double* u0, double tol, int32_t max_it, double* phi, double* dphi,
+                    hobi_solve_info* info) {
+  return solve_impl(h, u0, true, tol, max_it, phi, dphi, info);
 }
 
 int hobi_set_solution(hobi_t h, const double* u) {

@@ -34,7 +34,7 @@ KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
 
 EXPORTS = [
     "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
-    "hobi_solve", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
+    "hobi_solve", "hobi_solve_from", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
     "hobi_reaction_potential_noalloc", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_matvec.argtypes = [vp, dp, dp]
     lib.hobi_rhs.argtypes = [vp, dp]
     lib.hobi_solve.argtypes = [vp, C.c_double, C.c_int32, dp, dp, C.POINTER(SolveInfo)]
+    lib.hobi_solve_from.argtypes = [vp, dp, C.c_double, C.c_int32, dp, dp, C.POINTER(SolveInfo)]
     lib.hobi_set_solution.argtypes = [vp, dp]
     lib.hobi_get_solution.argtypes = [vp, dp]
     lib.hobi_reaction_potential.argtypes = [vp, dp, i64, dp]
@@ -242,8 +243,11 @@ class Solver:
         _check(self._lib.hobi_rhs(self._h, self._ptr(out)))
         return out
 
-    def solve(self, tol: float = 1e-6, max_it: int = 200, history: int = 0, raise_on_fail: bool = True):
-        """Returns (phi, dphi, info dict). info['status'] holds the return code."""
+    def solve(self, tol: float = 1e-6, max_it: int = 200, history: int = 0, raise_on_fail: bool = True,
+              u0=None, resume: bool = False):
+        """Returns (phi, dphi, info dict). info['status'] holds the return code. With u0 (an initial
+        guess [phi; dphi]) or resume=True (start from the handle's current solution) GMRES is warm
+        started (hobi_solve_from)."""
         phi = self._out(self.npts)
         dphi = self._out(self.npts)
         info = SolveInfo()
@@ -252,8 +256,16 @@ class Solver:
             hist = (C.c_double * history)()
             info.resid_history = C.cast(hist, C.POINTER(C.c_double))
             info.resid_capacity = history
-        code = self._lib.hobi_solve(self._h, float(tol), int(max_it), self._ptr(phi), self._ptr(dphi),
-                                    C.byref(info))
+        if u0 is not None or resume:
+            u0p = None
+            if u0 is not None:
+                self._u0_keep = self._in(u0, 2 * self.npts)  # alive until the call returns
+                u0p = self._ptr(self._u0_keep)
+            code = self._lib.hobi_solve_from(self._h, u0p, float(tol), int(max_it), self._ptr(phi), self._ptr(dphi),
+                                             C.byref(info))
+        else:
+            code = self._lib.hobi_solve(self._h, float(tol), int(max_it), self._ptr(phi), self._ptr(dphi),
+                                        C.byref(info))
         if raise_on_fail and code not in (HOBI_OK,):
             _check(code)
         d = {"status": code, "iterations": info.iterations, "converged": bool(info.converged),

@@ -329,3 +329,25 @@ def test_autotuner_decides_once_per_size(problems):
     assert ia["tuned"] and ib["tuned"] and ia["shape"] == ib["shape"]
     c = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp32", autotune=False)
     assert not c.plan_info()["tuned"]
+
+
+def test_warm_start_resumes_and_checkpoint(problems):
+    """Resume: a solve stopped at 1e-3 continued to 1e-6 reaches the oracle solution; a converged
+    initial guess (a saved checkpoint of u) returns after 0 iterations."""
+    p = problems["c2_l4"]
+    orc = p[-1]
+    u_ref, it_ref, _, _ = orc.gmres(1e-8)
+    s = _solver(p, "fp64")
+    _, _, i1 = s.solve(1e-3)
+    phi, dphi, i2 = s.solve(1e-6, resume=True)
+    assert i2["converged"] and i1["iterations"] + i2["iterations"] <= it_ref + 3
+    assert _rel(np.concatenate([phi, dphi]), u_ref) <= 1e-5
+    saved = s.solution()
+    t = _solver(p, "fp64")
+    phi3, dphi3, i3 = t.solve(1e-6, u0=saved)
+    assert i3["iterations"] == 0 and i3["converged"]
+    assert np.array_equal(np.concatenate([phi3, dphi3]), saved)
+    fresh = _solver(p, "fp64")
+    with pytest.raises(hobi.HobiError) as ei:
+        fresh.solve(1e-6, resume=True)
+    assert ei.value.code == hobi.HOBI_ERR_STATE
