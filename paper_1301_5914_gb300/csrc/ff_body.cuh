@@ -29,14 +29,64 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 
 __device__ __forceinline__ float2 pair_of(float a) { return make_float2(a, a); }
 
+// ---- source-tile pipeline: 1D bulk asynchronous copies (TMA) completing on mbarriers
+constexpr int kMaxBarrierSpins = 1 << 20;  // bounded waits: about a second, then report and stop
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Called by one thread, then __syncthreads(): two single-arrival barriers for the two tile stages.
+__device__ __forceinline__ void tile_barriers_init(unsigned long long* bars) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[0])) : "memory");
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[1])) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: copy `bytes` (multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory; completion is signalled on `bar` together with the expected byte count.
+__device__ __forceinline__ void tile_copy(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of dst come first
+  asm volatile(
+      "{\n\t.reg .b64 state;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 state, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Wait until the barrier's phase with the given parity has completed; false after the spin bound.
+__device__ __forceinline__ bool tile_wait(unsigned long long* bar, uint32_t parity) {
+  for (int i = 0; i < kMaxBarrierSpins; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // One block's share of the FP32 far field: NT threads, 2 TP targets per thread (targets
 // bx*NT*2TP ...), against source tiles [t0, t1) of TILE nodes; results (FP64) to out[i] (row 1)
-// and out[nt + i] (row 2). sh: 4 TILE float4 of shared memory. SKIP_SELF: a pair at zero
-// distance (a collocation point that is also a source node, LOBI-PB) contributes nothing.
+// and out[nt + i] (row 2). SKIP_SELF: a pair at zero distance (a collocation point that is also
+// a source node, LOBI-PB) contributes nothing.
+// Tiles stream through two shared-memory stages (sh: 2 x 4 TILE float4) by bulk asynchronous
+// copies issued by thread 0, each stage with its mbarrier (bars, initialised by
+// tile_barriers_init); `phases` carries the two barriers' parities across calls of one block.
+// If a barrier wait exceeds its bound, *err is set, in-flight copies are awaited (bounded) and
+// false is returned without writing outputs.
 template <bool ROW2, bool SKIP_SELF = false, int NT = kFF32Threads, int TP = kFF32Targets / 2, int TILE = kTile>
-__device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src,
+__device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src,
                                            int t0, int t1, float neg_kl2e, float kap, float eps,
-                                           double* __restrict__ out, int bx, float4* sh) {
+                                           double* __restrict__ out, int bx, float4* sh,
+                                           unsigned long long* bars, uint32_t& phases, int* err) {
+  constexpr uint32_t kTileBytes = 4 * TILE * sizeof(float4);
   constexpr int T = 2 * TP;
   float2 px[TP], py[TP], pz[TP];  // target k = 2p + lane
   float qx[T], qy[T], qz[T];
@@ -56,17 +106,29 @@ __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int n
   }
   const float2 nk2 = pair_of(neg_kl2e), kap2 = pair_of(kap), eps2 = pair_of(eps);
   const float2 m1 = pair_of(-1.f), three = pair_of(3.f), m3 = pair_of(-3.f);
-  for (int tile = t0; tile < t1; ++tile) {
-    __syncthreads();
-    const float4* g = src + (size_t)tile * (4 * TILE);
-    for (int q = threadIdx.x; q < 4 * TILE; q += NT) sh[q] = g[q];
-    __syncthreads();
+  const int ntile = t1 - t0;
+  __syncthreads();  // the stages are free (a previous call of this block has consumed them)
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 2 && k < ntile; ++k)
+      tile_copy(sh + k * 4 * TILE, src + (size_t)(t0 + k) * (4 * TILE), kTileBytes, &bars[k]);
+  for (int kt = 0; kt < ntile; ++kt) {  // kt: tile of this call
+    const int stage = kt & 1;
+    const bool ok = tile_wait(&bars[stage], (phases >> stage) & 1u);
+    if (__syncthreads_or(!ok)) {  // a copy never completed: report, drain, stop
+      if (threadIdx.x == 0) {
+        atomicOr(err, 1);
+        for (int j = kt; j < ntile && j < kt + 2; ++j) tile_wait(&bars[j & 1], (phases >> (j & 1)) & 1u);
+      }
+      return false;
+    }
+    phases ^= 1u << stage;
+    const float4* cur = sh + stage * 4 * TILE;
     float2 a1[TP], wx[TP], wy[TP], wz[TP];
 #pragma unroll
     for (int k = 0; k < TP; ++k) a1[k] = wx[k] = wy[k] = wz[k] = pair_of(0.f);
 #pragma unroll 2
     for (int s = 0; s < TILE; ++s) {
-      const float4 A = sh[4 * s], B = sh[4 * s + 1], C = sh[4 * s + 2], D = sh[4 * s + 3];
+      const float4 A = cur[4 * s], B = cur[4 * s + 1], C = cur[4 * s + 2], D = cur[4 * s + 3];
       const float2 nyx = make_float2(A.x, A.y), nyy = make_float2(A.z, A.w), nyz = make_float2(B.x, B.y);
       const float2 sg = make_float2(B.z, B.w), mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w);
       const float2 mz = make_float2(D.x, D.y), se = make_float2(D.z, D.w);
@@ -114,6 +176,9 @@ __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int n
                     fmaf(qx[2 * k + 1], wx[k].y, fmaf(qy[2 * k + 1], wy[k].y, qz[2 * k + 1] * wz[k].y)));
       }
     }
+    __syncthreads();  // every thread has finished reading this stage
+    if (threadIdx.x == 0 && kt + 2 < ntile)
+      tile_copy(sh + stage * 4 * TILE, src + (size_t)(t0 + kt + 2) * (4 * TILE), kTileBytes, &bars[stage]);
   }
 #pragma unroll
   for (int k = 0; k < T; ++k) {
@@ -123,6 +188,7 @@ __device__ __forceinline__ void ff32_block(const float4* __restrict__ tgt, int n
       if (ROW2) out[nt + i] = (double)h2[k] + (double)l2[k];
     }
   }
+  return true;
 }
 
 // One block's share of the FP64 far field (2 targets per thread); sh: 4 kTile double2.

@@ -64,6 +64,7 @@ struct hobi_ctx {
   // nv: collocation points (mesh vertices for HOBI, face centroids for LOBI); nv_mesh: mesh vertices
   int64_t nv = 0, nf = 0, nc = 0, n_nodes = 0, n_pad = 0, nv_mesh = 0;
   int* zero_ptr = nullptr;  // LOBI: an all-zero incidence row pointer (no singular correction)
+  int* ff_err = nullptr;    // far-field tile pipeline timeout flag (device)
   double eps1 = 1, eps2 = 80, kappa = 0, eps = 80;
   int num_sms = 1;
   std::vector<void*> allocs;
@@ -160,6 +161,17 @@ struct hobi_ctx {
     if (!mem_device) HOBI_CK(cudaStreamSynchronize(stream));
     return HOBI_OK;
   }
+  // A far-field tile pipeline that timed out leaves the result incomplete: report it.
+  int check_farfield() {
+    int flag = 0;
+    HOBI_CK(cudaMemcpyAsync(&flag, ff_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    HOBI_CK(cudaStreamSynchronize(stream));
+    if (flag) {
+      HOBI_CK(cudaMemsetAsync(ff_err, 0, sizeof(int), stream));
+      return fail(HOBI_ERR_CUDA, "far-field source-tile pipeline timed out (a bulk copy did not complete)");
+    }
+    return HOBI_OK;
+  }
 
   // --------------------------------------------------------------- matvec pipeline
   int farfield(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, double* out,
@@ -170,7 +182,7 @@ struct hobi_ctx {
       for (int q = 0; q < 2; ++q)
         if (!gev[pi][q]) HOBI_CK(cudaEventCreate(&gev[pi][q]));
       HOBI_CK(cudaEventRecordWithFlags(gev[pi][0], stream, cudaEventRecordExternal));
-      HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream, skip_self));
+      HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, ff_err, stream, skip_self));
       HOBI_CK(cudaEventRecordWithFlags(gev[pi][1], stream, cudaEventRecordExternal));
       graph_pairs[pi] = (double)p.n_targets * (double)n_nodes;
       return HOBI_OK;
@@ -187,7 +199,7 @@ struct hobi_ctx {
       ++prof_used;
       HOBI_CK(cudaEventRecord(a, stream));
     }
-    HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, stream, skip_self));
+    HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, ff_err, stream, skip_self));
     if (prof) {
       HOBI_CK(cudaEventRecord(bb, stream));
       pending_pairs += (double)p.n_targets * (double)n_nodes;
@@ -450,6 +462,8 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_TRY(h->alloc(&h->center_part, 3 * kValidateBlocks));
   HOBI_TRY(h->alloc(&h->center, 3));
   HOBI_TRY(h->alloc(&h->flags, 1));
+  HOBI_TRY(h->alloc(&h->ff_err, 1));
+  HOBI_CK(cudaMemsetAsync(h->ff_err, 0, sizeof(int), h->stream));
   HOBI_CK(cudaMemcpyAsync(h->V, vertices, sizeof(double) * 3 * nv, kind, h->stream));
   HOBI_CK(cudaMemcpyAsync(h->Nin, normals, sizeof(double) * 3 * nv, kind, h->stream));
   HOBI_CK(cudaMemcpyAsync(h->F, faces, sizeof(int32_t) * 3 * nf, kind, h->stream));
@@ -559,7 +573,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
         for (int rep = 0; rep < 2; ++rep) {
           HOBI_CK(cudaEventRecord(h->ev_t0, h->stream));
           HOBI_CK(launch_farfield(true, cand[sh], h->tgt32, h->tgt64, h->src32, h->src64, h->eps, h->kappa, h->part,
-                                  h->stream, skip));
+                                  h->ff_err, h->stream, skip));
           HOBI_CK(cudaEventRecord(h->ev_t1, h->stream));
           HOBI_CK(cudaEventSynchronize(h->ev_t1));
           float ms = 0.f;
@@ -572,6 +586,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
           shape = sh;
         }
       }
+      HOBI_TRY(h->check_farfield());
       tune_store(key, shape);
       h->tuned = 1;
     }
@@ -743,7 +758,7 @@ int hobi_matvec(hobi_t h, const double* u, double* Au) {
   if (!h->mem_device) HOBI_CK(cudaMemcpyAsync(Au, ad, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
   HOBI_TRY(h->finish());
   HOBI_TRY(h->collect_profile());
-  return HOBI_OK;
+  return h->check_farfield();
 }
 
 int hobi_rhs(hobi_t h, double* b) {
@@ -825,6 +840,7 @@ int solve_impl(hobi_t h, const double* u0, bool warm, double tol, int32_t max_it
   HOBI_TRY(h->finish());
   HOBI_CK(cudaEventSynchronize(h->ev_t1));
   HOBI_TRY(h->collect_profile());
+  HOBI_TRY(h->check_farfield());
   h->have_solution = true;
   const GmresState fs = *h->st_host;
   if (info) {
@@ -893,7 +909,7 @@ int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, do
   HOBI_TRY(h->copy_out(phi, h->phi_pts, n_points));
   HOBI_TRY(h->finish());
   HOBI_TRY(h->collect_profile());
-  return HOBI_OK;
+  return h->check_farfield();
 }
 
 int hobi_energy(hobi_t h, double* e_sol) {
@@ -913,6 +929,7 @@ int hobi_energy(hobi_t h, double* e_sol) {
   HOBI_TRY(h->leave());
   HOBI_CK(cudaStreamSynchronize(h->stream));
   HOBI_TRY(h->collect_profile());
+  HOBI_TRY(h->check_farfield());
   *e_sol = *h->host_scalar;
   return HOBI_OK;
 }
@@ -1061,11 +1078,12 @@ extern "C" int hobi_reaction_potential_noalloc(hobi_t h, const double* points, i
   HOBI_TRY(h->copy_in(pts, points, 3 * n));
   HOBI_CK(launch_points((int)n, pts, 3, h->center, t32, t64, h->stream));
   HOBI_TRY(h->gather(fp32, h->x, nullptr, 0));
-  HOBI_CK(launch_farfield(fp32, p, t32, t64, h->src32, h->src64, h->eps, h->kappa, part, h->stream));
+  HOBI_CK(launch_farfield(fp32, p, t32, t64, h->src32, h->src64, h->eps, h->kappa, part, h->ff_err, h->stream));
   HOBI_CK(launch_reduce_points((int)n, p.chunks, part, phi_d, h->stream));
   h->launches += 4;
   HOBI_TRY(h->copy_out(phi, phi_d, n));
-  return h->finish();
+  HOBI_TRY(h->finish());
+  return h->check_farfield();
 }
 
 // =============================================================================================
@@ -1080,6 +1098,7 @@ struct hobi_batch_ctx {
   int nmol = 0;
   std::vector<hobi_t> subs;
   std::vector<MolDesc> mols_h;
+  int* ff_err = nullptr;  // far-field tile pipeline timeout flag (device)
   std::vector<int64_t> vert_off_h, node_off_h, charge_off_h;
   int64_t N = 0, total_nodes = 0, total_verts = 0;
   std::vector<void*> allocs;
@@ -1161,7 +1180,7 @@ struct hobi_batch_ctx {
       HOBI_CK(cudaEventRecordWithFlags(pev[0], stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     }
     HOBI_CK(launch_farfield_batch(fp32, mols, tasks[fp32], ntasks[fp32], counter, mask, eps, kappa, ff_grid[fp32],
-                                  stream));
+                                  ff_err, stream));
     if (prof) {
       HOBI_CK(cudaEventRecordWithFlags(pev[1], stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
       if (!capturing) {
@@ -1235,6 +1254,16 @@ struct hobi_batch_ctx {
     HOBI_TRY(prof_collect());
     HOBI_CK(cudaMemcpyAsync(ms_host, ms, sizeof(MolState) * nmol, cudaMemcpyDeviceToHost, stream));
     HOBI_CK(cudaStreamSynchronize(stream));
+    return HOBI_OK;
+  }
+  int check_farfield() {
+    int flag = 0;
+    HOBI_CK(cudaMemcpyAsync(&flag, ff_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    HOBI_CK(cudaStreamSynchronize(stream));
+    if (flag) {
+      HOBI_CK(cudaMemsetAsync(ff_err, 0, sizeof(int), stream));
+      return fail(HOBI_ERR_CUDA, "far-field source-tile pipeline timed out (a bulk copy did not complete)");
+    }
     return HOBI_OK;
   }
   bool all_done() const {
@@ -1353,6 +1382,8 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   HOBI_TRY(B->alloc(&B->node_off, nmol + 1));
   HOBI_TRY(B->alloc(&B->vert_off, nmol + 1));
   HOBI_TRY(B->alloc(&B->counter, 1));
+  HOBI_TRY(B->alloc(&B->ff_err, 1));
+  HOBI_CK(cudaMemsetAsync(B->ff_err, 0, sizeof(int), B->stream));
   HOBI_CK(cudaMemcpyAsync(B->mols, B->mols_h.data(), sizeof(MolDesc) * nmol, cudaMemcpyHostToDevice, B->stream));
   HOBI_CK(cudaMemcpyAsync(B->seg, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice, B->stream));
   HOBI_CK(cudaMemcpyAsync(B->mol_seg, mol_seg.data(), sizeof(int) * (nmol + 1), cudaMemcpyHostToDevice, B->stream));
@@ -1496,7 +1527,7 @@ int hobi_matvec_batch(hobi_batch_t B, const double* u, double* Au) {
   HOBI_TRY(B->leave());
   HOBI_CK(cudaStreamSynchronize(B->stream));
   HOBI_TRY(B->prof_collect());
-  return HOBI_OK;
+  return B->check_farfield();
 }
 
 int hobi_solve_batch(hobi_batch_t B, double tol, int32_t max_it, double* phi, double* dphi, int32_t* iterations,
@@ -1552,6 +1583,7 @@ int hobi_solve_batch(hobi_batch_t B, double tol, int32_t max_it, double* phi, do
   }
   HOBI_TRY(B->leave());
   HOBI_CK(cudaStreamSynchronize(B->stream));
+  HOBI_TRY(B->check_farfield());
   B->have_solution = true;
   int n_conv = 0, n_break = 0;
   double worst = 0.0;

@@ -97,10 +97,12 @@ struct FarFieldPlan {
 FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2, int num_sms,
                            int blocks_per_sm, int shape = 0);
 int farfield_blocks_per_sm(bool fp32, bool row2, int shape = 0);
-// skip_self: pairs at zero distance contribute nothing (LOBI-PB, where targets are source nodes)
+// skip_self: pairs at zero distance contribute nothing (LOBI-PB, where targets are source nodes).
+// err: device flag set to nonzero if the FP32 kernel's tile pipeline timed out (then the partial
+// sums are incomplete and the call must be reported as failed).
 cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt32, const double* tgt64,
                             const float4* src32, const double* src64, double eps, double kappa,
-                            double* part, cudaStream_t s, bool skip_self = false);
+                            double* part, int* err, cudaStream_t s, bool skip_self = false);
 // LOBI-PB node densities (one node per face)
 cudaError_t launch_gather_lobi(bool fp32, int nf, const double* ny, const double* nnu, const double* nW,
                                const double* center, const double* u, const int* kptr, int64_t ld, double inv_eps,
@@ -181,7 +183,7 @@ constexpr int kTilesPerTask = 16;
 cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const int64_t* node_off, int64_t total_nodes,
                                 const double* u, const int* kptr, int64_t ld, const MolState* ms, cudaStream_t s);
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,
-                                  const MolState* ms, double eps, double kappa, int grid, cudaStream_t s);
+                                  const MolState* ms, double eps, double kappa, int grid, int* err, cudaStream_t s);
 int farfield_batch_blocks_per_sm(bool fp32);
 cudaError_t launch_combine_batch(const MolDesc* mols, int nmol, const int64_t* vert_off, int64_t total_verts,
                                  const double* u, const int* kptr, int64_t ld, double* Au, const MolState* ms,

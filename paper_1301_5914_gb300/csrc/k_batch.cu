@@ -70,9 +70,13 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
 // depend on which block ran which task.
 __global__ void __launch_bounds__(kFF32Threads, 2)
     k_farfield_batch32(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, int ntasks, int* counter,
-                       const MolState* ms, float neg_kl2e, float kap, float eps) {
-  __shared__ float4 sh[4 * kTile];
+                       const MolState* ms, float neg_kl2e, float kap, float eps, int* err) {
+  __shared__ __align__(128) float4 sh[2 * 4 * kTile];
+  __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_task;
+  if (threadIdx.x == 0) ff::tile_barriers_init(bars);
+  __syncthreads();
+  uint32_t phases = 0;  // barrier parities, carried from task to task
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
     __syncthreads();
@@ -82,12 +86,15 @@ __global__ void __launch_bounds__(kFF32Threads, 2)
     const FFTask tk = tasks[t];
     if (mol_done(ms, tk.mol)) continue;
     const MolDesc& d = mols[tk.mol];
+    bool ok;
     if (tk.narrow)  // small molecules: 512 targets per block wastes fewer idle lanes
-      ff::ff32_block<true, false, kFF32Threads, 1, kTile>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap, eps,
-                                                          d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh);
+      ok = ff::ff32_block<true, false, kFF32Threads, 1, kTile>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap,
+                                                               eps, d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh,
+                                                               bars, phases, err);
     else
-      ff::ff32_block<true>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap, eps,
-                           d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh);
+      ok = ff::ff32_block<true>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap, eps,
+                                d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh, bars, phases, err);
+    if (!ok) return;  // the tile pipeline timed out (reported through err)
   }
 }
 
@@ -315,11 +322,12 @@ cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const 
 }
 
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,
-                                  const MolState* ms, double eps, double kappa, int grid, cudaStream_t s) {
+                                  const MolState* ms, double eps, double kappa, int grid, int* err, cudaStream_t s) {
   cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (fp32)
     k_farfield_batch32<<<grid, kFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms,
-                                                    (float)(-kappa * 1.4426950408889634074), (float)kappa, (float)eps);
+                                                    (float)(-kappa * 1.4426950408889634074), (float)kappa, (float)eps,
+                                                    err);
   else
     k_farfield_batch64<<<grid, kFF64Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, kappa, eps);
   return cudaGetLastError();

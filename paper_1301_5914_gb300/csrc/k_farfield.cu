@@ -79,11 +79,15 @@ __global__ void k_pad(int n_nodes, int n_pad, float4* src32, double* src64) {
 template <bool ROW2, bool SKIP_SELF, int NT, int TP, int TILE>
 __global__ void __launch_bounds__(NT, 512 / NT)
     k_farfield32(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src, int n_tiles, int tpc,
-                 float neg_kl2e, float kap, float eps, double* __restrict__ part, int64_t ldp) {
-  __shared__ float4 sh[4 * TILE];
+                 float neg_kl2e, float kap, float eps, double* __restrict__ part, int64_t ldp, int* err) {
+  __shared__ __align__(128) float4 sh[2 * 4 * TILE];
+  __shared__ __align__(8) unsigned long long bars[2];
+  if (threadIdx.x == 0) ff::tile_barriers_init(bars);
+  __syncthreads();
+  uint32_t phases = 0;
   const int t0 = blockIdx.y * tpc;
   ff::ff32_block<ROW2, SKIP_SELF, NT, TP, TILE>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), neg_kl2e, kap, eps,
-                       part + (size_t)blockIdx.y * ldp, blockIdx.x, sh);
+                                                part + (size_t)blockIdx.y * ldp, blockIdx.x, sh, bars, phases, err);
 }
 
 template <bool ROW2, bool SKIP_SELF = false>
@@ -166,19 +170,21 @@ constexpr FF32Shape kShapes[kNumFF32Shapes] = {{256, 2, 256}, {128, 2, 128}, {12
 
 template <bool ROW2, bool SKIP>
 cudaError_t launch32_shape(int shape, dim3 grid, const float4* tgt, int nt, const float4* src, int n_tiles, int tpc,
-                           float nk, float kap, float eps, double* part, int64_t ldp, cudaStream_t s) {
+                           float nk, float kap, float eps, double* part, int64_t ldp, int* err, cudaStream_t s) {
   switch (shape) {
     case 1:
-      k_farfield32<ROW2, SKIP, 128, 2, 128><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+      k_farfield32<ROW2, SKIP, 128, 2, 128>
+          <<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
       break;
     case 2:
-      k_farfield32<ROW2, SKIP, 128, 1, 64><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+      k_farfield32<ROW2, SKIP, 128, 1, 64><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
       break;
     case 3:
-      k_farfield32<ROW2, SKIP, 64, 1, 64><<<grid, 64, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+      k_farfield32<ROW2, SKIP, 64, 1, 64><<<grid, 64, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
       break;
     default:
-      k_farfield32<ROW2, SKIP, 256, 2, 256><<<grid, 256, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp);
+      k_farfield32<ROW2, SKIP, 256, 2, 256>
+          <<<grid, 256, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
   }
   return cudaGetLastError();
 }
@@ -247,7 +253,7 @@ FarFieldPlan plan_farfield(bool fp32, int n_targets, int n_nodes_pad, bool row2,
 
 cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt32, const double* tgt64,
                             const float4* src32, const double* src64, double eps, double kappa, double* part,
-                            cudaStream_t s, bool skip_self) {
+                            int* err, cudaStream_t s, bool skip_self) {
   const int64_t ldp = p.row2 ? 2 * (int64_t)p.n_targets : (int64_t)p.n_targets;
   if (fp32) {
     const FF32Shape& sh = kShapes[p.shape];
@@ -256,12 +262,12 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
     const float nk = (float)(-kappa * 1.4426950408889634074);
     if (p.row2 && skip_self)
       return launch32_shape<true, true>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
-                                        (float)kappa, (float)eps, part, ldp, s);
+                                        (float)kappa, (float)eps, part, ldp, err, s);
     if (p.row2)
       return launch32_shape<true, false>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
-                                         (float)kappa, (float)eps, part, ldp, s);
+                                         (float)kappa, (float)eps, part, ldp, err, s);
     return launch32_shape<false, false>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
-                                        (float)kappa, (float)eps, part, ldp, s);
+                                        (float)kappa, (float)eps, part, ldp, err, s);
   }
   dim3 grid((p.n_targets + kFF64Threads * kFF64Targets - 1) / (kFF64Threads * kFF64Targets), p.chunks);
   if (p.row2 && skip_self)
