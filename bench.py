@@ -58,7 +58,10 @@ WORKLOAD = WORKLOAD_C2
 MOLECULE = {"eps1": 2.0, "eps2": 80.0, "kappa": 0.1257, "gmres_tol": 1e-6,
             "precision": WORKLOAD_C2["precision"],
             "surface": "Gaussian-density isosurface (marching tetrahedra, smoothed), density-gradient normals"}
-OPS_PER_PAIR = 36  # FP32 FMA-pipe instructions per pair in the both-rows far-field kernel
+# FP32 FMA-pipe operations per pair in the both-rows far-field kernel as written (kappa > 0:
+# 6 for d and r^2, 3 for d.m, 3 for 1/r^2, 1/r^3 and v, 2 for 1 + kappa r and the exp2 argument,
+# 1 for P - 1, 4 for row 1, 3 for S, 2 for the 1/r^3 factors, 6 for the vector accumulation)
+OPS_PER_PAIR = 30
 MUFU_PER_PAIR = 2  # rsqrt.approx + ex2.approx
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "farfield32_c2_ico6_traffic.txt")
 FARFIELD_SRC = [os.path.join(ROOT, "paper_1301_5914_gb300", "csrc", f) for f in ("k_farfield.cu", "ff_body.cuh")]

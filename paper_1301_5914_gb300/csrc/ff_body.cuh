@@ -75,19 +75,21 @@ __device__ __forceinline__ bool tile_wait(unsigned long long* bar, uint32_t pari
 // One block's share of the FP32 far field: NT threads, 2 TP targets per thread (targets
 // bx*NT*2TP ...), against source tiles [t0, t1) of TILE nodes; results (FP64) to out[i] (row 1)
 // and out[nt + i] (row 2). SKIP_SELF: a pair at zero distance (a collocation point that is also
-// a source node, LOBI-PB) contributes nothing.
+// a source node, LOBI-PB) contributes nothing. KS: coordinates and m are stored multiplied by
+// kappa (FF32Consts), so kappa r is the scaled distance itself.
 // Tiles stream through two shared-memory stages (sh: 2 x 4 TILE float4) by bulk asynchronous
 // copies issued by thread 0, each stage with its mbarrier (bars, initialised by
 // tile_barriers_init); `phases` carries the two barriers' parities across calls of one block.
 // If a barrier wait exceeds its bound, *err is set, in-flight copies are awaited (bounded) and
 // false is returned without writing outputs.
-template <bool ROW2, bool SKIP_SELF = false, int NT = kFF32Threads, int TP = kFF32Targets / 2, int TILE = kTile>
+template <bool ROW2, bool KS, bool SKIP_SELF = false, int NT = kFF32Threads, int TP = kFF32Targets / 2,
+          int TILE = kTile>
 __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src,
-                                           int t0, int t1, float neg_kl2e, float kap, float eps,
-                                           double* __restrict__ out, int bx, float4* sh,
-                                           unsigned long long* bars, uint32_t& phases, int* err) {
+                                           int t0, int t1, const FF32Consts& cs, double* __restrict__ out, int bx,
+                                           float4* sh, unsigned long long* bars, uint32_t& phases, int* err) {
   constexpr uint32_t kTileBytes = 4 * TILE * sizeof(float4);
   constexpr int T = 2 * TP;
+  constexpr int kUnroll = TP >= 4 ? 1 : 2;  // 4 packed pairs already give enough independent chains
   float2 px[TP], py[TP], pz[TP];  // target k = 2p + lane
   float qx[T], qy[T], qz[T];
   float h1[T], l1[T], h2[T], l2[T];
@@ -104,8 +106,11 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
     qx[k] = b.x; qy[k] = b.y; qz[k] = b.z;
     h1[k] = l1[k] = h2[k] = l2[k] = 0.f;
   }
-  const float2 nk2 = pair_of(neg_kl2e), kap2 = pair_of(kap), eps2 = pair_of(eps);
-  const float2 m1 = pair_of(-1.f), three = pair_of(3.f), m3 = pair_of(-3.f);
+  constexpr float kLog2e = 1.4426950408889634f;
+  const float2 one = pair_of(1.f), m1 = pair_of(-1.f), m3 = pair_of(-3.f);
+  const float2 l2e = pair_of(kLog2e), nl2e = pair_of(-kLog2e);
+  const float2 kap2 = pair_of(cs.kap), nk2 = pair_of(cs.neg_kl2e), kk2 = pair_of(cs.kap_sq);
+  const float2 omie = pair_of(cs.one_minus_inv_eps);
   const int ntile = t1 - t0;
   __syncthreads();  // the stages are free (a previous call of this block has consumed them)
   if (threadIdx.x == 0)
@@ -126,40 +131,47 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
     float2 a1[TP], wx[TP], wy[TP], wz[TP];
 #pragma unroll
     for (int k = 0; k < TP; ++k) a1[k] = wx[k] = wy[k] = wz[k] = pair_of(0.f);
-#pragma unroll 2
+#pragma unroll kUnroll
     for (int s = 0; s < TILE; ++s) {
       const float4 A = cur[4 * s], B = cur[4 * s + 1], C = cur[4 * s + 2], D = cur[4 * s + 3];
       const float2 nyx = make_float2(A.x, A.y), nyy = make_float2(A.z, A.w), nyz = make_float2(B.x, B.y);
-      const float2 sg = make_float2(B.z, B.w), mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w);
-      const float2 mz = make_float2(D.x, D.y), se = make_float2(D.z, D.w);
+      const float2 se = make_float2(B.z, B.w), mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w);
+      const float2 mz = make_float2(D.x, D.y), sd = make_float2(D.z, D.w);
 #pragma unroll
       for (int k = 0; k < TP; ++k) {
         const float2 dx = __fadd2_rn(px[k], nyx), dy = __fadd2_rn(py[k], nyy), dz = __fadd2_rn(pz[k], nyz);
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-        if (SKIP_SELF) {  // 1/r -> 0 before r is formed: every term of the pair then vanishes
+        if (SKIP_SELF) {  // 1/r -> 0 before anything else: every term of the pair then vanishes
           ir.x = r2.x > 0.f ? ir.x : 0.f;
           ir.y = r2.y > 0.f ? ir.y : 0.f;
         }
-        const float2 r = __fmul2_rn(r2, ir);
-        const float2 ea = __fmul2_rn(nk2, r);
-        const float2 E = make_float2(exp2_approx(ea.x), exp2_approx(ea.y));
         const float2 aym = __ffma2_rn(dz, mz, __ffma2_rn(dy, my, __fmul2_rn(dx, mx)));  // d . m
         const float2 ir2 = __fmul2_rn(ir, ir);
-        const float2 ir3 = __fmul2_rn(ir2, ir);
-        const float2 u3 = __fmul2_rn(aym, ir3);                                       // (d . m)/r^3
-        const float2 kr = __fmul2_rn(kap2, r);
-        const float2 P = __ffma2_rn(E, kr, E);
-        // row 1: (1 - E)/r sigma + (eps P - 1)(d . m)/r^3
-        a1[k] = __ffma2_rn(__ffma2_rn(make_float2(-E.x, -E.y), ir, ir), sg, a1[k]);
-        a1[k] = __ffma2_rn(__ffma2_rn(eps2, P, m1), u3, a1[k]);
+        const float2 v = __fmul2_rn(aym, ir2);  // (d . m)/r^2
+        float2 r1, ea;                          // 1 + kappa r, -kappa r log2(e)
+        if (KS) {
+          r1 = __ffma2_rn(r2, ir, one);
+          ea = __ffma2_rn(nl2e, r1, l2e);
+        } else {
+          const float2 r = __fmul2_rn(r2, ir);
+          r1 = __ffma2_rn(kap2, r, one);
+          ea = __fmul2_rn(nk2, r);
+        }
+        const float2 E = make_float2(exp2_approx(ea.x), exp2_approx(ea.y));
+        const float2 nE = make_float2(-E.x, -E.y);
+        const float2 Pm1 = __ffma2_rn(E, r1, m1);  // P - 1
+        // row 1 / eps = [ (1 - E) sigma/eps + (P - 1/eps)(d . m)/r^2 ] / r
+        const float2 g = __ffma2_rn(nE, se, se);
+        a1[k] = __ffma2_rn(__ffma2_rn(__fadd2_rn(Pm1, omie), v, g), ir, a1[k]);
         if (ROW2) {
-          const float2 Q3 = __ffma2_rn(E, __ffma2_rn(kr, __fadd2_rn(kr, three), three), m3);  // Q - 3
-          const float2 w = __ffma2_rn(P, ir3, make_float2(-ir3.x, -ir3.y));                  // (P - 1)/r^3
-          const float2 q2 = __fmul2_rn(Q3, ir2);
-          // (P/eps - 1) sigma / r^3 - (Q - 3)(d . m)/r^5
-          const float2 sv = __ffma2_rn(make_float2(-q2.x, -q2.y), u3,
-                                       __fmul2_rn(__ffma2_rn(P, se, make_float2(-sg.x, -sg.y)), ir3));
+          const float2 ir3 = __fmul2_rn(ir2, ir);
+          // S = (P/eps - 1) sigma - (Q - 3)(d . m)/r^2, with Q - 3 = 3 (P - 1) + E (kappa r)^2 and
+          // r^2 (d . m)/r^2 = d . m:  S = (P - 1)(sigma/eps - 3 v) + (sigma/eps - sigma) - E kappa^2 (d . m)
+          const float2 t = __ffma2_rn(Pm1, __ffma2_rn(m3, v, se), sd);
+          const float2 S = __ffma2_rn(KS ? nE : __fmul2_rn(nE, kk2), aym, t);
+          const float2 w = __fmul2_rn(Pm1, ir3);  // (P - 1)/r^3
+          const float2 sv = __fmul2_rn(S, ir3);
           wx[k] = __ffma2_rn(w, mx, __ffma2_rn(sv, dx, wx[k]));
           wy[k] = __ffma2_rn(w, my, __ffma2_rn(sv, dy, wy[k]));
           wz[k] = __ffma2_rn(w, mz, __ffma2_rn(sv, dz, wz[k]));
@@ -184,8 +196,8 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
   for (int k = 0; k < T; ++k) {
     int i = base + k * NT;
     if (i < nt) {
-      out[i] = (double)h1[k] + (double)l1[k];
-      if (ROW2) out[nt + i] = (double)h2[k] + (double)l2[k];
+      out[i] = ((double)h1[k] + (double)l1[k]) * cs.row1_scale;
+      if (ROW2) out[nt + i] = ((double)h2[k] + (double)l2[k]) * cs.row2_scale;
     }
   }
   return true;
@@ -248,11 +260,12 @@ __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int n
 
 // Node densities of the iterate u for one node (Sec. 2.2, W_{j,m,n} with linear density
 // interpolation): sigma = sum_n W u_{N_v+v_n}/4pi, mu = sum_n W u_{v_n}/4pi; the FP32 layout
-// stores each value twice for the paired arithmetic: {-y}, {sigma}, {m = mu nu_y}, {sigma/eps}.
+// stores each value twice for the paired arithmetic: {-xs y}, {sigma/eps}, {m = xs mu nu_y},
+// {sigma/eps - sigma}, where xs is the far field's coordinate scale (ff32_coord_scale).
 __device__ __forceinline__ void gather32_node(int node, int nv, const int* __restrict__ F,
                                               const double* __restrict__ ny, const double* __restrict__ nnu,
                                               const double* __restrict__ nW, const double* __restrict__ center,
-                                              const double* __restrict__ u, double inv_eps,
+                                              const double* __restrict__ u, double inv_eps, double xs,
                                               float4* __restrict__ src) {
   int j = node >> 2;
   int a = F[3 * j], b = F[3 * j + 1], c = F[3 * j + 2];
@@ -261,14 +274,16 @@ __device__ __forceinline__ void gather32_node(int node, int nv, const int* __res
   double mu = (W[0] * u[a] + W[1] * u[b] + W[2] * u[c]) * kInv4Pi;
   const double* y = ny + 3 * (size_t)node;
   const double* n = nnu + 3 * (size_t)node;
-  const float yx = (float)(center[0] - y[0]), yy = (float)(center[1] - y[1]), yz = (float)(center[2] - y[2]);
-  const float sg = (float)sig, se = (float)(sig * inv_eps);
-  const float mx = (float)(mu * n[0]), my = (float)(mu * n[1]), mz = (float)(mu * n[2]);
+  const float yx = (float)(xs * (center[0] - y[0])), yy = (float)(xs * (center[1] - y[1])),
+              yz = (float)(xs * (center[2] - y[2]));
+  const float se = (float)(sig * inv_eps), sd = (float)(sig * inv_eps - sig);
+  const double xm = xs * mu;
+  const float mx = (float)(xm * n[0]), my = (float)(xm * n[1]), mz = (float)(xm * n[2]);
   float4* o = src + 4 * (size_t)node;
   o[0] = make_float4(yx, yx, yy, yy);
-  o[1] = make_float4(yz, yz, sg, sg);
+  o[1] = make_float4(yz, yz, se, se);
   o[2] = make_float4(mx, mx, my, my);
-  o[3] = make_float4(mz, mz, se, se);
+  o[3] = make_float4(mz, mz, sd, sd);
 }
 
 __device__ __forceinline__ void gather64_node(int node, int nv, const int* __restrict__ F,
@@ -298,19 +313,21 @@ __device__ __forceinline__ void gather64_node(int node, int nv, const int* __res
 __device__ __forceinline__ void gather32_lobi(int j, int nf, const double* __restrict__ ny,
                                               const double* __restrict__ nnu, const double* __restrict__ nW,
                                               const double* __restrict__ center, const double* __restrict__ u,
-                                              double inv_eps, float4* __restrict__ src) {
+                                              double inv_eps, double xs, float4* __restrict__ src) {
   const double A = nW[3 * (size_t)j];
   const double sig = A * u[nf + j] * kInv4Pi, mu = A * u[j] * kInv4Pi;
   const double* y = ny + 3 * (size_t)j;
   const double* n = nnu + 3 * (size_t)j;
-  const float yx = (float)(center[0] - y[0]), yy = (float)(center[1] - y[1]), yz = (float)(center[2] - y[2]);
-  const float sg = (float)sig, se = (float)(sig * inv_eps);
-  const float mx = (float)(mu * n[0]), my = (float)(mu * n[1]), mz = (float)(mu * n[2]);
+  const float yx = (float)(xs * (center[0] - y[0])), yy = (float)(xs * (center[1] - y[1])),
+              yz = (float)(xs * (center[2] - y[2]));
+  const float se = (float)(sig * inv_eps), sd = (float)(sig * inv_eps - sig);
+  const double xm = xs * mu;
+  const float mx = (float)(xm * n[0]), my = (float)(xm * n[1]), mz = (float)(xm * n[2]);
   float4* o = src + 4 * (size_t)j;
   o[0] = make_float4(yx, yx, yy, yy);
-  o[1] = make_float4(yz, yz, sg, sg);
+  o[1] = make_float4(yz, yz, se, se);
   o[2] = make_float4(mx, mx, my, my);
-  o[3] = make_float4(mz, mz, se, se);
+  o[3] = make_float4(mz, mz, sd, sd);
 }
 
 __device__ __forceinline__ void gather64_lobi(int j, int nf, const double* __restrict__ ny,

@@ -66,6 +66,7 @@ struct hobi_ctx {
   int* zero_ptr = nullptr;  // LOBI: an all-zero incidence row pointer (no singular correction)
   int* ff_err = nullptr;    // far-field tile pipeline timeout flag (device)
   double eps1 = 1, eps2 = 80, kappa = 0, eps = 80;
+  double xs = 1;            // coordinate scale of the FP32 tables (ff32_coord_scale(kappa))
   int num_sms = 1;
   std::vector<void*> allocs;
   // inputs and geometry
@@ -210,9 +211,10 @@ struct hobi_ctx {
   // node densities of u (scheme-dependent node layout)
   int gather(bool fp32, const double* u, const int* kptr, int64_t ld) {
     if (scheme == HOBI_SCHEME_LOBI)
-      HOBI_CK(launch_gather_lobi(fp32, (int)nf, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps, src32, src64, stream));
+      HOBI_CK(launch_gather_lobi(fp32, (int)nf, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps, xs, src32, src64,
+                                 stream));
     else
-      HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps,
+      HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps, xs,
                             src32, src64, stream));
     return HOBI_OK;
   }
@@ -502,8 +504,8 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
     HOBI_CK(cudaMemsetAsync(h->zero_ptr, 0, sizeof(int) * (nf + 1), h->stream));
     HOBI_CK(launch_lobi_geometry((int)nf, h->F, h->V, h->ny, h->nnu, h->nW, h->flags, h->stream));
     HOBI_CK(launch_rhs((int)nf, (int)nc, h->ny, h->nnu, h->Q, h->eps1, h->b, h->stream));
-    HOBI_CK(launch_targets((int)nf, h->ny, h->nnu, h->center, h->tgt32, h->tgt64, h->stream));
-    HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
+    HOBI_CK(launch_targets((int)nf, h->ny, h->nnu, h->center, h->xs, h->tgt32, h->tgt64, h->stream));
+    HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->xs, h->ctgt32, h->ctgt64, h->stream));
     HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
     h->launches += 3 + (nc > 0 ? 1 : 0) + (h->n_pad > h->n_nodes ? 1 : 0);
   } else {
@@ -526,8 +528,8 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
     HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem, h->ny,
                                       h->nnu, h->nW, h->eps, h->kappa, h->corr, h->stream));
     HOBI_CK(launch_rhs((int)nv, (int)nc, h->V, h->Nv, h->Q, h->eps1, h->b, h->stream));
-    HOBI_CK(launch_targets((int)nv, h->V, h->Nv, h->center, h->tgt32, h->tgt64, h->stream));
-    HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->ctgt32, h->ctgt64, h->stream));
+    HOBI_CK(launch_targets((int)nv, h->V, h->Nv, h->center, h->xs, h->tgt32, h->tgt64, h->stream));
+    HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->xs, h->ctgt32, h->ctgt64, h->stream));
     HOBI_CK(launch_pad_sources((int)h->n_nodes, (int)h->n_pad, h->src32, h->src64, h->stream));
     h->launches += 4 + (nc > 0 ? 1 : 0) + (h->n_pad > h->n_nodes ? 1 : 0);
   }
@@ -685,6 +687,7 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   h->eps1 = eps1;
   h->eps2 = eps2;
   h->kappa = kappa;
+  h->xs = ff32_coord_scale(kappa);
   h->eps = eps2 / eps1;
   int r = HOBI_OK;
   do {
@@ -903,7 +906,7 @@ int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, do
   HOBI_TRY(h->enter());
   HOBI_TRY(h->ensure_point_buffers(n_points));
   HOBI_TRY(h->copy_in(h->pts_in, points, 3 * n_points));
-  HOBI_CK(launch_points((int)n_points, h->pts_in, 3, h->center, h->ptgt32, h->ptgt64, h->stream));
+  HOBI_CK(launch_points((int)n_points, h->pts_in, 3, h->center, h->xs, h->ptgt32, h->ptgt64, h->stream));
   h->launches += 1;
   HOBI_TRY(h->reaction_dev(n_points, h->ptgt32, h->ptgt64, h->phi_pts));
   HOBI_TRY(h->copy_out(phi, h->phi_pts, n_points));
@@ -1076,7 +1079,7 @@ extern "C" int hobi_reaction_potential_noalloc(hobi_t h, const double* points, i
   // scratch left over from an earlier call needs no clearing
   HOBI_TRY(h->enter());
   HOBI_TRY(h->copy_in(pts, points, 3 * n));
-  HOBI_CK(launch_points((int)n, pts, 3, h->center, t32, t64, h->stream));
+  HOBI_CK(launch_points((int)n, pts, 3, h->center, h->xs, t32, t64, h->stream));
   HOBI_TRY(h->gather(fp32, h->x, nullptr, 0));
   HOBI_CK(launch_farfield(fp32, p, t32, t64, h->src32, h->src64, h->eps, h->kappa, part, h->ff_err, h->stream));
   HOBI_CK(launch_reduce_points((int)n, p.chunks, part, phi_d, h->stream));
@@ -1326,7 +1329,7 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
     d.F = h->F; d.ny = h->ny; d.nnu = h->nnu; d.nW = h->nW; d.center = h->center;
     d.inc_ptr = h->inc_ptr; d.inc_face = h->inc_face; d.corr = h->corr;
     d.tgt32 = h->tgt32; d.tgt64 = h->tgt64; d.src32 = h->src32; d.src64 = h->src64;
-    d.nv = (int)h->nv; d.n_nodes = (int)h->n_nodes; d.eps = h->eps;
+    d.nv = (int)h->nv; d.n_nodes = (int)h->n_nodes; d.eps = h->eps; d.xs = h->xs;
     d.u_off = B->N;
     const int n_tiles = (int)(h->n_pad / kTile);
     d.chunks = (n_tiles + kTilesPerTask - 1) / kTilesPerTask;
@@ -1335,12 +1338,12 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
       int per_block = fp32 ? kFF32Threads * kFF32Targets : kFF64Threads * kFF64Targets;
       int narrow = 0;
       if (fp32) {
-        // 2 targets per thread when the padding of the last 1024-target block costs more than the
-        // narrower block's ~4 % lower throughput
+        // half the targets per thread (512 per block) when the padding of the last 1024-target
+        // block costs more than the narrower block's ~4 % lower throughput
         const int64_t pad4 = (h->nv + 1023) / 1024 * 1024, pad2 = (h->nv + 511) / 512 * 512;
         if ((double)pad2 * 1.04 < (double)pad4) {
           narrow = 1;
-          per_block = kFF32Threads * 2;
+          per_block = kFF32Threads * kFF32Targets / 2;
         }
       }
       const int tt = (int)((h->nv + per_block - 1) / per_block);
@@ -1363,7 +1366,7 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
     HOBI_TRY(B->alloc(&B->tasks[fp32], tl[fp32].size()));
     HOBI_CK(cudaMemcpyAsync(B->tasks[fp32], tl[fp32].data(), sizeof(FFTask) * tl[fp32].size(), cudaMemcpyHostToDevice,
                             B->stream));
-    B->ff_grid[fp32] = B->num_sms * farfield_batch_blocks_per_sm(fp32);
+    B->ff_grid[fp32] = B->num_sms * farfield_batch_blocks_per_sm(fp32, B->kappa);
   }
   // segments of the concatenated vector
   std::vector<Segment> segs;

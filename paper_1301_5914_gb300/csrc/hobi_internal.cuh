@@ -7,9 +7,10 @@
 //                                                              node index = 4 j + m (FP64)
 //   inc_ptr[n_v+1], inc_face[3 n_f]                            vertex -> incident faces (sorted)
 //   corr[3 n_f][3][4]         singular correction per (vertex, incident face) entry (FP64)
-//   tgt32[n_v][2] float4      target x - c and unit normal (FP32 path)
+//   tgt32[n_v][2] float4      target xs (x - c) and unit normal (FP32 path)
 //   src32[n_pad][4] float4    per node, each value twice for paired FP32 math, rebuilt per matvec:
-//                             {-y}, {sigma}, {m = mu nu_y}, {sigma/eps} (y relative to c; sigma, mu / 4pi)
+//                             {-xs y}, {sigma/eps}, {m = xs mu nu_y}, {sigma/eps - sigma}
+//                             (y relative to c; sigma, mu / 4pi; xs = ff32_coord_scale(kappa))
 //   src64[n_pad][8] double    (y - c, sigma/4pi, mu nu_y/4pi, 0) per node (FP64 path)
 //   part[chunks][2 n_v]       FP64 far-field partial sums per source chunk
 // c is the vertex centroid: both precisions work in coordinates relative to it.
@@ -25,8 +26,10 @@ constexpr double kInv4Pi = 1.0 / (4.0 * 3.14159265358979323846);
 constexpr double kCoulomb = 332.0716;  // kcal A / (mol e^2)
 
 // Far-field tiling (FP32): threads per block, targets per thread, source nodes per smem tile.
-constexpr int kFF32Threads = 256;
-constexpr int kFF32Targets = 4;
+// 8 targets per thread (4 packed pairs) with 2 blocks of 128 threads per SM: fewer warps, but
+// more independent pair chains per warp, which hides the MUFU and FMA latencies better.
+constexpr int kFF32Threads = 128;
+constexpr int kFF32Targets = 8;
 constexpr int kTile = 256;
 // FP64 path
 constexpr int kFF64Threads = 128;
@@ -69,9 +72,35 @@ cudaError_t launch_lobi_geometry(int nf, const int* F, const double* V, double* 
                                  int* flags, cudaStream_t s);
 cudaError_t launch_rhs(int nv, int nc, const double* V, const double* Nv, const double* Q, double eps1,
                        double* b, cudaStream_t s);
-cudaError_t launch_targets(int nv, const double* V, const double* Nv, const double* center, float4* tgt32,
-                           double* tgt64, cudaStream_t s);
-cudaError_t launch_points(int np, const double* P, int stride, const double* center, float4* tgt32,
+// FP32 far-field coordinate scale. For kappa >= kKappaScaledMin the FP32 tables hold coordinates
+// (and m) multiplied by kappa, so the kernel's kappa r is the scaled distance itself and the row
+// sums are rescaled once per target; below it (kappa = 0 included) they are stored unscaled. The
+// bound keeps kappa r far inside the FP32 range for any distance above 1e-6 A.
+constexpr double kKappaScaledMin = 1e-6;
+inline bool ff32_kappa_scaled(double kappa) { return kappa >= kKappaScaledMin; }
+inline double ff32_coord_scale(double kappa) { return ff32_kappa_scaled(kappa) ? kappa : 1.0; }
+// Per-launch constants of the FP32 pair arithmetic (row 1 is summed divided by eps).
+struct FF32Consts {
+  float kap, neg_kl2e, kap_sq;  // unscaled mode: kappa, -kappa log2(e), kappa^2
+  float one_minus_inv_eps;      // 1 - 1/eps
+  double row1_scale;            // eps xs
+  double row2_scale;            // xs^2
+};
+inline FF32Consts ff32_consts(double eps, double kappa) {
+  const double xs = ff32_coord_scale(kappa);
+  FF32Consts c;
+  c.kap = (float)kappa;
+  c.neg_kl2e = (float)(-kappa * 1.4426950408889634074);
+  c.kap_sq = (float)(kappa * kappa);
+  c.one_minus_inv_eps = (float)(1.0 - 1.0 / eps);
+  c.row1_scale = eps * xs;
+  c.row2_scale = xs * xs;
+  return c;
+}
+// xs: ff32_coord_scale(kappa), applied to the FP32 copies only.
+cudaError_t launch_targets(int nv, const double* V, const double* Nv, const double* center, double xs,
+                           float4* tgt32, double* tgt64, cudaStream_t s);
+cudaError_t launch_points(int np, const double* P, int stride, const double* center, double xs, float4* tgt32,
                           double* tgt64, cudaStream_t s);
 
 // ---- far field (k_farfield.cu) ----
@@ -79,11 +108,11 @@ cudaError_t launch_points(int np, const double* P, int stride, const double* cen
 // If kptr != nullptr the vector is u + (*kptr) * ld (GMRES basis column).
 cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
-                          const int* kptr, int64_t ld, double inv_eps, float4* src32, double* src64,
+                          const int* kptr, int64_t ld, double inv_eps, double xs, float4* src32, double* src64,
                           cudaStream_t s);
 cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* src64, cudaStream_t s);
 
-// FP32 far-field block shapes (threads, targets per thread, source tile): 0 = 256 x 4, tile 256;
+// FP32 far-field block shapes (threads, targets per thread, source tile): 0 = 128 x 8, tile 256;
 // 1 = 128 x 4, tile 128; 2 = 128 x 2, tile 64; 3 = 64 x 2, tile 64 (small problems).
 constexpr int kNumFF32Shapes = 4;
 struct FarFieldPlan {
@@ -106,7 +135,7 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
 // LOBI-PB node densities (one node per face)
 cudaError_t launch_gather_lobi(bool fp32, int nf, const double* ny, const double* nnu, const double* nW,
                                const double* center, const double* u, const int* kptr, int64_t ld, double inv_eps,
-                               float4* src32, double* src64, cudaStream_t s);
+                               double xs, float4* src32, double* src64, cudaStream_t s);
 // Au = diag u - (sum of chunk partials + singular correction)  (rows i and n_v + i)
 cudaError_t launch_combine(int nv, int chunks, const double* part, const int* F, const int* inc_ptr,
                            const int* inc_face, const double* corr, double eps, const double* u,
@@ -158,11 +187,12 @@ struct MolDesc {          // one molecule's device tables (owned by its single-m
   double* part;           // [chunks][2 nv] partials of the batched far field
   int nv, n_nodes, chunks;
   double eps;
+  double xs;              // FP32 coordinate scale (ff32_coord_scale)
   int64_t u_off;          // offset of the molecule's 2 nv block in the concatenated vectors
 };
 struct FFTask {           // one persistent far-field work item
   int mol, bx, t0, t1, chunk;
-  int narrow;             // FP32: 1 = 2 targets per thread (512 per block), 0 = 4 (1024 per block)
+  int narrow;             // FP32: 1 = 4 targets per thread (512 per block), 0 = 8 (1024 per block)
 };
 struct Segment {          // piece of the concatenated vector inside one molecule
   int64_t start;
@@ -184,7 +214,7 @@ cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const 
                                 const double* u, const int* kptr, int64_t ld, const MolState* ms, cudaStream_t s);
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,
                                   const MolState* ms, double eps, double kappa, int grid, int* err, cudaStream_t s);
-int farfield_batch_blocks_per_sm(bool fp32);
+int farfield_batch_blocks_per_sm(bool fp32, double kappa);
 cudaError_t launch_combine_batch(const MolDesc* mols, int nmol, const int64_t* vert_off, int64_t total_verts,
                                  const double* u, const int* kptr, int64_t ld, double* Au, const MolState* ms,
                                  cudaStream_t s);

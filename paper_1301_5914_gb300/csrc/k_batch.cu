@@ -59,7 +59,7 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
   const double* um = u + (kptr ? (int64_t)(*kptr) * ld : 0) + d.u_off;
   int node = (int)(g - node_off[m]);
   if (fp32)
-    ff::gather32_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.src32);
+    ff::gather32_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.xs, d.src32);
   else
     ff::gather64_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, d.src64);
 }
@@ -68,9 +68,10 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
 // from an atomic counter (reset to 0 before each launch) until the list is exhausted; tasks of
 // converged molecules are skipped. Each task writes its own partial slot, so the result does not
 // depend on which block ran which task.
+template <bool KS>
 __global__ void __launch_bounds__(kFF32Threads, 2)
     k_farfield_batch32(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, int ntasks, int* counter,
-                       const MolState* ms, float neg_kl2e, float kap, float eps, int* err) {
+                       const MolState* ms, FF32Consts cs, int* err) {
   __shared__ __align__(128) float4 sh[2 * 4 * kTile];
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_task;
@@ -88,12 +89,12 @@ __global__ void __launch_bounds__(kFF32Threads, 2)
     const MolDesc& d = mols[tk.mol];
     bool ok;
     if (tk.narrow)  // small molecules: 512 targets per block wastes fewer idle lanes
-      ok = ff::ff32_block<true, false, kFF32Threads, 1, kTile>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap,
-                                                               eps, d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh,
-                                                               bars, phases, err);
+      ok = ff::ff32_block<true, KS, false, kFF32Threads, kFF32Targets / 4, kTile>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs,
+                                                                   d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh,
+                                                                   bars, phases, err);
     else
-      ok = ff::ff32_block<true>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, neg_kl2e, kap, eps,
-                                d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh, bars, phases, err);
+      ok = ff::ff32_block<true, KS>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs, d.part + (size_t)tk.chunk * 2 * d.nv,
+                                    tk.bx, sh, bars, phases, err);
     if (!ok) return;  // the tile pipeline timed out (reported through err)
   }
 }
@@ -324,19 +325,23 @@ cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const 
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,
                                   const MolState* ms, double eps, double kappa, int grid, int* err, cudaStream_t s) {
   cudaMemsetAsync(counter, 0, sizeof(int), s);
-  if (fp32)
-    k_farfield_batch32<<<grid, kFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms,
-                                                    (float)(-kappa * 1.4426950408889634074), (float)kappa, (float)eps,
-                                                    err);
+  if (fp32 && ff32_kappa_scaled(kappa))
+    k_farfield_batch32<true><<<grid, kFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
+                                                          err);
+  else if (fp32)
+    k_farfield_batch32<false><<<grid, kFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
+                                                           err);
   else
     k_farfield_batch64<<<grid, kFF64Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, kappa, eps);
   return cudaGetLastError();
 }
 
-int farfield_batch_blocks_per_sm(bool fp32) {
+int farfield_batch_blocks_per_sm(bool fp32, double kappa) {
   int n = 1;
-  if (fp32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32, kFF32Threads, 0);
+  if (fp32 && ff32_kappa_scaled(kappa))
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32<true>, kFF32Threads, 0);
+  else if (fp32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32<false>, kFF32Threads, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch64, kFF64Threads, 0);
   return n > 0 ? n : 1;

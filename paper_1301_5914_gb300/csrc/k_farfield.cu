@@ -13,7 +13,7 @@
 // accumulation instead of two dot products. Faces incident to x_i are included here and
 // replaced by the singular rule through the precomputed correction (combine kernel).
 //
-// FP32-bulk kernel: each thread keeps 4 targets in registers as two packed pairs and evaluates
+// FP32-bulk kernel: each thread keeps 8 targets in registers as four packed pairs and evaluates
 // every pair formula with Blackwell's paired FP32 instructions (__ffma2_rn / __fmul2_rn /
 // __fadd2_rn: one instruction = the same operation on two targets), which halves the issue
 // slots of the FMA-pipe work so that the FMA pipe itself becomes the limit. 256-node source
@@ -21,6 +21,15 @@
 // feeds two packed operands; rsqrt and exp2 go to the MUFU pipe (rsqrt.approx / ex2.approx).
 // Each tile's FP32 sum is folded into a compensated (two-float) accumulator, and the result is
 // written as FP64 per (source chunk, target); the combine kernel adds the chunks in a fixed order.
+//
+// FP32 evaluation order (30 FMA-pipe operations per pair). With kappa > 0 the FP32 tables hold
+// kappa x, kappa y and kappa m, so that kappa r is the scaled r; with v = (d . m)/r^2,
+// P - 1 = E (1 + kappa r) - 1 and Q - 3 = 3 (P - 1) + E (kappa r)^2 (and r^2 v = d . m):
+//   row 1 / eps = [ (1 - E) sigma/eps + (P - 1 + 1 - 1/eps) v ] / r
+//   S = (P - 1)(sigma/eps - 3 v) + (sigma/eps - sigma) - E kappa^2 (d . m)
+//   row 2 vector += (P - 1)/r^3 m + S/r^3 d
+// which is the pair formula above multiplied out; the scale factors (eps kappa for row 1,
+// kappa^2 for row 2) are applied once per target to the FP64 result.
 #include <math.h>
 
 #include "ff_body.cuh"
@@ -32,11 +41,11 @@ namespace {
 __global__ void k_gather32(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
                            const double* __restrict__ nnu, const double* __restrict__ nW,
                            const double* __restrict__ center, const double* __restrict__ u, const int* kptr,
-                           int64_t ld, double inv_eps, float4* __restrict__ src) {
+                           int64_t ld, double inv_eps, double xs, float4* __restrict__ src) {
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= n_nodes) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
-  ff::gather32_node(node, nv, F, ny, nnu, nW, center, u, inv_eps, src);
+  ff::gather32_node(node, nv, F, ny, nnu, nW, center, u, inv_eps, xs, src);
 }
 
 __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
@@ -52,12 +61,12 @@ __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const
 __global__ void k_gather_lobi(bool fp32, int nf, const double* __restrict__ ny, const double* __restrict__ nnu,
                               const double* __restrict__ nW, const double* __restrict__ center,
                               const double* __restrict__ u, const int* kptr, int64_t ld, double inv_eps,
-                              float4* __restrict__ src32, double* __restrict__ src64) {
+                              double xs, float4* __restrict__ src32, double* __restrict__ src64) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nf) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
   if (fp32)
-    ff::gather32_lobi(j, nf, ny, nnu, nW, center, u, inv_eps, src32);
+    ff::gather32_lobi(j, nf, ny, nnu, nW, center, u, inv_eps, xs, src32);
   else
     ff::gather64_lobi(j, nf, ny, nnu, nW, center, u, src64);
 }
@@ -76,18 +85,25 @@ __global__ void k_pad(int n_nodes, int n_pad, float4* src32, double* src64) {
 }
 
 // ------------------------------------------------------------------ far field kernels
-template <bool ROW2, bool SKIP_SELF, int NT, int TP, int TILE>
-__global__ void __launch_bounds__(NT, 512 / NT)
+// resident blocks per SM the register budget is sized for: 512 threads, or 256 with 8 targets each
+template <int NT, int TP>
+constexpr int ff32_min_blocks() {
+  return (TP >= 4 ? 256 : 512) / NT;
+}
+
+template <bool ROW2, bool KS, bool SKIP_SELF, int NT, int TP, int TILE>
+__global__ void __launch_bounds__(NT, ff32_min_blocks<NT, TP>())
     k_farfield32(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src, int n_tiles, int tpc,
-                 float neg_kl2e, float kap, float eps, double* __restrict__ part, int64_t ldp, int* err) {
+                 FF32Consts cs, double* __restrict__ part, int64_t ldp, int* err) {
   __shared__ __align__(128) float4 sh[2 * 4 * TILE];
   __shared__ __align__(8) unsigned long long bars[2];
   if (threadIdx.x == 0) ff::tile_barriers_init(bars);
   __syncthreads();
   uint32_t phases = 0;
   const int t0 = blockIdx.y * tpc;
-  ff::ff32_block<ROW2, SKIP_SELF, NT, TP, TILE>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), neg_kl2e, kap, eps,
-                                                part + (size_t)blockIdx.y * ldp, blockIdx.x, sh, bars, phases, err);
+  ff::ff32_block<ROW2, KS, SKIP_SELF, NT, TP, TILE>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), cs,
+                                                    part + (size_t)blockIdx.y * ldp, blockIdx.x, sh, bars, phases,
+                                                    err);
 }
 
 template <bool ROW2, bool SKIP_SELF = false>
@@ -140,10 +156,11 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
-                          const int* kptr, int64_t ld, double inv_eps, float4* src32, double* src64,
+                          const int* kptr, int64_t ld, double inv_eps, double xs, float4* src32, double* src64,
                           cudaStream_t s) {
   if (fp32)
-    k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, src32);
+    k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, xs,
+                                                  src32);
   else
     k_gather64<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, src64);
   return cudaGetLastError();
@@ -151,8 +168,9 @@ cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const do
 
 cudaError_t launch_gather_lobi(bool fp32, int nf, const double* ny, const double* nnu, const double* nW,
                                const double* center, const double* u, const int* kptr, int64_t ld, double inv_eps,
-                               float4* src32, double* src64, cudaStream_t s) {
-  k_gather_lobi<<<nblk(nf, 256), 256, 0, s>>>(fp32, nf, ny, nnu, nW, center, u, kptr, ld, inv_eps, src32, src64);
+                               double xs, float4* src32, double* src64, cudaStream_t s) {
+  k_gather_lobi<<<nblk(nf, 256), 256, 0, s>>>(fp32, nf, ny, nnu, nW, center, u, kptr, ld, inv_eps, xs, src32,
+                                              src64);
   return cudaGetLastError();
 }
 
@@ -166,25 +184,23 @@ cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* sr
 struct FF32Shape {
   int nt, tp, tile;
 };
-constexpr FF32Shape kShapes[kNumFF32Shapes] = {{256, 2, 256}, {128, 2, 128}, {128, 1, 64}, {64, 1, 64}};
+constexpr FF32Shape kShapes[kNumFF32Shapes] = {{128, 4, 256}, {128, 2, 128}, {128, 1, 64}, {64, 1, 64}};
 
-template <bool ROW2, bool SKIP>
+template <bool ROW2, bool KS, bool SKIP>
 cudaError_t launch32_shape(int shape, dim3 grid, const float4* tgt, int nt, const float4* src, int n_tiles, int tpc,
-                           float nk, float kap, float eps, double* part, int64_t ldp, int* err, cudaStream_t s) {
+                           const FF32Consts& cs, double* part, int64_t ldp, int* err, cudaStream_t s) {
   switch (shape) {
     case 1:
-      k_farfield32<ROW2, SKIP, 128, 2, 128>
-          <<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 128, 2, 128><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
       break;
     case 2:
-      k_farfield32<ROW2, SKIP, 128, 1, 64><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 128, 1, 64><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
       break;
     case 3:
-      k_farfield32<ROW2, SKIP, 64, 1, 64><<<grid, 64, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 64, 1, 64><<<grid, 64, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
       break;
     default:
-      k_farfield32<ROW2, SKIP, 256, 2, 256>
-          <<<grid, 256, 0, s>>>(tgt, nt, src, n_tiles, tpc, nk, kap, eps, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 128, 4, 256><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
   }
   return cudaGetLastError();
 }
@@ -194,16 +210,16 @@ int occupancy32(int shape) {
   int n = 1;
   switch (shape) {
     case 1:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 128, 2, 128>, 128, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 128, 2, 128>, 128, 0);
       break;
     case 2:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 128, 1, 64>, 128, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 128, 1, 64>, 128, 0);
       break;
     case 3:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 64, 1, 64>, 64, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 64, 1, 64>, 64, 0);
       break;
     default:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, SKIP, 256, 2, 256>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 128, 4, 256>, 128, 0);
   }
   return n > 0 ? n : 1;
 }
@@ -259,15 +275,17 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
     const FF32Shape& sh = kShapes[p.shape];
     const int per_block = sh.nt * 2 * sh.tp;
     dim3 grid((p.n_targets + per_block - 1) / per_block, p.chunks);
-    const float nk = (float)(-kappa * 1.4426950408889634074);
+    const FF32Consts cs = ff32_consts(eps, kappa);
+    const bool ks = ff32_kappa_scaled(kappa);
+    const int nt = p.n_targets, nti = p.n_tiles, tpc = p.tiles_per_chunk;
     if (p.row2 && skip_self)
-      return launch32_shape<true, true>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
-                                        (float)kappa, (float)eps, part, ldp, err, s);
+      return ks ? launch32_shape<true, true, true>(p.shape, grid, tgt32, nt, src32, nti, tpc, cs, part, ldp, err, s)
+                : launch32_shape<true, false, true>(p.shape, grid, tgt32, nt, src32, nti, tpc, cs, part, ldp, err, s);
     if (p.row2)
-      return launch32_shape<true, false>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
-                                         (float)kappa, (float)eps, part, ldp, err, s);
-    return launch32_shape<false, false>(p.shape, grid, tgt32, p.n_targets, src32, p.n_tiles, p.tiles_per_chunk, nk,
-                                        (float)kappa, (float)eps, part, ldp, err, s);
+      return ks ? launch32_shape<true, true, false>(p.shape, grid, tgt32, nt, src32, nti, tpc, cs, part, ldp, err, s)
+                : launch32_shape<true, false, false>(p.shape, grid, tgt32, nt, src32, nti, tpc, cs, part, ldp, err, s);
+    return ks ? launch32_shape<false, true, false>(p.shape, grid, tgt32, nt, src32, nti, tpc, cs, part, ldp, err, s)
+              : launch32_shape<false, false, false>(p.shape, grid, tgt32, nt, src32, nti, tpc, cs, part, ldp, err, s);
   }
   dim3 grid((p.n_targets + kFF64Threads * kFF64Targets - 1) / (kFF64Threads * kFF64Targets), p.chunks);
   if (p.row2 && skip_self)

@@ -430,23 +430,24 @@ __global__ void k_rhs(int nv, int nc, const double* V, const double* Nv, const d
 }
 
 // ------------------------------------------------------------------ targets
-__global__ void k_targets(int nv, const double* V, const double* Nv, const double* center, float4* t32,
+__global__ void k_targets(int nv, const double* V, const double* Nv, const double* center, double xs, float4* t32,
                           double* t64) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv) return;
   double3 x = ld3(V + 3 * i) - ld3(center), n = ld3(Nv + 3 * i);
-  t32[2 * i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+  t32[2 * i] = make_float4((float)(xs * x.x), (float)(xs * x.y), (float)(xs * x.z), 0.f);
   t32[2 * i + 1] = make_float4((float)n.x, (float)n.y, (float)n.z, 0.f);
   double* o = t64 + 8 * (size_t)i;
   o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = 0.0;
   o[4] = n.x; o[5] = n.y; o[6] = n.z; o[7] = 0.0;
 }
 
-__global__ void k_points(int np, const double* P, int stride, const double* center, float4* t32, double* t64) {
+__global__ void k_points(int np, const double* P, int stride, const double* center, double xs, float4* t32,
+                         double* t64) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   double3 x = ld3(P + (size_t)stride * i) - ld3(center);
-  t32[2 * i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+  t32[2 * i] = make_float4((float)(xs * x.x), (float)(xs * x.y), (float)(xs * x.z), 0.f);
   t32[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
   double* o = t64 + 8 * (size_t)i;
   o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = 0.0;
@@ -528,16 +529,16 @@ cudaError_t launch_rhs(int nv, int nc, const double* V, const double* Nv, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_targets(int nv, const double* V, const double* Nv, const double* center, float4* tgt32,
-                           double* tgt64, cudaStream_t s) {
-  k_targets<<<nblk(nv, 256), 256, 0, s>>>(nv, V, Nv, center, tgt32, tgt64);
+cudaError_t launch_targets(int nv, const double* V, const double* Nv, const double* center, double xs,
+                           float4* tgt32, double* tgt64, cudaStream_t s) {
+  k_targets<<<nblk(nv, 256), 256, 0, s>>>(nv, V, Nv, center, xs, tgt32, tgt64);
   return cudaGetLastError();
 }
 
-cudaError_t launch_points(int np, const double* P, int stride, const double* center, float4* tgt32,
+cudaError_t launch_points(int np, const double* P, int stride, const double* center, double xs, float4* tgt32,
                           double* tgt64, cudaStream_t s) {
   if (np <= 0) return cudaSuccess;
-  k_points<<<nblk(np, 256), 256, 0, s>>>(np, P, stride, center, tgt32, tgt64);
+  k_points<<<nblk(np, 256), 256, 0, s>>>(np, P, stride, center, xs, tgt32, tgt64);
   return cudaGetLastError();
 }
 }  // namespace hobi
