@@ -1335,21 +1335,12 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
     d.chunks = (n_tiles + kTilesPerTask - 1) / kTilesPerTask;
     HOBI_TRY(B->alloc(&d.part, (size_t)d.chunks * 2 * h->nv));
     for (int fp32 = 0; fp32 < 2; ++fp32) {
-      int per_block = fp32 ? kFF32Threads * kFF32Targets : kFF64Threads * kFF64Targets;
-      int narrow = 0;
-      if (fp32) {
-        // half the targets per thread (512 per block) when the padding of the last 1024-target
-        // block costs more than the narrower block's ~4 % lower throughput
-        const int64_t pad4 = (h->nv + 1023) / 1024 * 1024, pad2 = (h->nv + 511) / 512 * 512;
-        if ((double)pad2 * 1.04 < (double)pad4) {
-          narrow = 1;
-          per_block = kFF32Threads * kFF32Targets / 2;
-        }
-      }
+      const int per_block = fp32 ? kBatchFF32Threads * kFF32Targets : kFF64Threads * kFF64Targets;
+      const int tiles = fp32 ? (int)(h->n_pad / kBatchFF32Tile) : n_tiles;
+      const int tpt = fp32 ? kBatchFF32TilesPerTask : kTilesPerTask;
       const int tt = (int)((h->nv + per_block - 1) / per_block);
       for (int bx = 0; bx < tt; ++bx)
-        for (int c = 0; c < d.chunks; ++c)
-          tl[fp32].push_back({m, bx, c * kTilesPerTask, std::min(n_tiles, (c + 1) * kTilesPerTask), c, narrow});
+        for (int c = 0; c < d.chunks; ++c) tl[fp32].push_back({m, bx, c * tpt, std::min(tiles, (c + 1) * tpt), c});
     }
     B->mols_h.push_back(d);
     B->N += 2 * h->nv;

@@ -113,7 +113,8 @@ cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const do
 cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* src64, cudaStream_t s);
 
 // FP32 far-field block shapes (threads, targets per thread, source tile): 0 = 128 x 8, tile 256;
-// 1 = 128 x 4, tile 128; 2 = 128 x 2, tile 64; 3 = 64 x 2, tile 64 (small problems).
+// 1 = 64 x 8, tile 128; 2 = 32 x 8, tile 64; 3 = 32 x 4, tile 64 (small problems). Targets per
+// block: 1024, 512, 256, 128.
 constexpr int kNumFF32Shapes = 4;
 struct FarFieldPlan {
   int n_targets;
@@ -190,9 +191,8 @@ struct MolDesc {          // one molecule's device tables (owned by its single-m
   double xs;              // FP32 coordinate scale (ff32_coord_scale)
   int64_t u_off;          // offset of the molecule's 2 nv block in the concatenated vectors
 };
-struct FFTask {           // one persistent far-field work item
+struct FFTask {           // one persistent far-field work item: targets of block bx, tiles [t0, t1)
   int mol, bx, t0, t1, chunk;
-  int narrow;             // FP32: 1 = 4 targets per thread (512 per block), 0 = 8 (1024 per block)
 };
 struct Segment {          // piece of the concatenated vector inside one molecule
   int64_t start;
@@ -209,7 +209,13 @@ struct MolState {
   double bnorm, rel, tol, hn;
 };
 constexpr int kSegLen = 4096;
-constexpr int kTilesPerTask = 16;
+constexpr int kTilesPerTask = 16;  // kTile-node tiles per task (FP64), i.e. 4096 source nodes
+// Batched FP32 far field: one-warp persistent blocks with 8 targets per thread (256 targets per
+// task, so a molecule wastes at most 255 target slots) and 64-node tiles, 64 of them per task
+// (the same 4096 source nodes per chunk as the FP64 tasks).
+constexpr int kBatchFF32Threads = 32;
+constexpr int kBatchFF32Tile = 64;
+constexpr int kBatchFF32TilesPerTask = kTilesPerTask * kTile / kBatchFF32Tile;
 cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const int64_t* node_off, int64_t total_nodes,
                                 const double* u, const int* kptr, int64_t ld, const MolState* ms, cudaStream_t s);
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,

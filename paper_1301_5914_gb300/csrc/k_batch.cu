@@ -69,10 +69,10 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
 // converged molecules are skipped. Each task writes its own partial slot, so the result does not
 // depend on which block ran which task.
 template <bool KS>
-__global__ void __launch_bounds__(kFF32Threads, 2)
+__global__ void __launch_bounds__(kBatchFF32Threads, 8)
     k_farfield_batch32(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, int ntasks, int* counter,
                        const MolState* ms, FF32Consts cs, int* err) {
-  __shared__ __align__(128) float4 sh[2 * 4 * kTile];
+  __shared__ __align__(128) float4 sh[2 * 4 * kBatchFF32Tile];
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_task;
   if (threadIdx.x == 0) ff::tile_barriers_init(bars);
@@ -87,14 +87,8 @@ __global__ void __launch_bounds__(kFF32Threads, 2)
     const FFTask tk = tasks[t];
     if (mol_done(ms, tk.mol)) continue;
     const MolDesc& d = mols[tk.mol];
-    bool ok;
-    if (tk.narrow)  // small molecules: 512 targets per block wastes fewer idle lanes
-      ok = ff::ff32_block<true, KS, false, kFF32Threads, kFF32Targets / 4, kTile>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs,
-                                                                   d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh,
-                                                                   bars, phases, err);
-    else
-      ok = ff::ff32_block<true, KS>(d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs, d.part + (size_t)tk.chunk * 2 * d.nv,
-                                    tk.bx, sh, bars, phases, err);
+    const bool ok = ff::ff32_block<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kBatchFF32Tile>(
+        d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs, d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh, bars, phases, err);
     if (!ok) return;  // the tile pipeline timed out (reported through err)
   }
 }
@@ -326,10 +320,10 @@ cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* 
                                   const MolState* ms, double eps, double kappa, int grid, int* err, cudaStream_t s) {
   cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (fp32 && ff32_kappa_scaled(kappa))
-    k_farfield_batch32<true><<<grid, kFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
+    k_farfield_batch32<true><<<grid, kBatchFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
                                                           err);
   else if (fp32)
-    k_farfield_batch32<false><<<grid, kFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
+    k_farfield_batch32<false><<<grid, kBatchFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
                                                            err);
   else
     k_farfield_batch64<<<grid, kFF64Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, kappa, eps);
@@ -339,9 +333,9 @@ cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* 
 int farfield_batch_blocks_per_sm(bool fp32, double kappa) {
   int n = 1;
   if (fp32 && ff32_kappa_scaled(kappa))
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32<true>, kFF32Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32<true>, kBatchFF32Threads, 0);
   else if (fp32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32<false>, kFF32Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32<false>, kBatchFF32Threads, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch64, kFF64Threads, 0);
   return n > 0 ? n : 1;

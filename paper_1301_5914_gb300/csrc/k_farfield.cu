@@ -180,24 +180,26 @@ cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* sr
 }
 
 // FP32 block shapes the planner and the autotuner choose from: threads, target pairs per thread,
-// source nodes per shared-memory tile. Shape 0 is the default for large problems.
+// source nodes per shared-memory tile. Shape 0 is the default for large problems; the smaller
+// blocks (down to one warp, each with its own tile pipeline) keep 8 targets per thread where
+// they can and give more blocks for problems with few targets.
 struct FF32Shape {
   int nt, tp, tile;
 };
-constexpr FF32Shape kShapes[kNumFF32Shapes] = {{128, 4, 256}, {128, 2, 128}, {128, 1, 64}, {64, 1, 64}};
+constexpr FF32Shape kShapes[kNumFF32Shapes] = {{128, 4, 256}, {64, 4, 128}, {32, 4, 64}, {32, 2, 64}};
 
 template <bool ROW2, bool KS, bool SKIP>
 cudaError_t launch32_shape(int shape, dim3 grid, const float4* tgt, int nt, const float4* src, int n_tiles, int tpc,
                            const FF32Consts& cs, double* part, int64_t ldp, int* err, cudaStream_t s) {
   switch (shape) {
     case 1:
-      k_farfield32<ROW2, KS, SKIP, 128, 2, 128><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 64, 4, 128><<<grid, 64, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
       break;
     case 2:
-      k_farfield32<ROW2, KS, SKIP, 128, 1, 64><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 32, 4, 64><<<grid, 32, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
       break;
     case 3:
-      k_farfield32<ROW2, KS, SKIP, 64, 1, 64><<<grid, 64, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 32, 2, 64><<<grid, 32, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
       break;
     default:
       k_farfield32<ROW2, KS, SKIP, 128, 4, 256><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
@@ -210,13 +212,13 @@ int occupancy32(int shape) {
   int n = 1;
   switch (shape) {
     case 1:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 128, 2, 128>, 128, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 64, 4, 128>, 64, 0);
       break;
     case 2:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 128, 1, 64>, 128, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 32, 4, 64>, 32, 0);
       break;
     case 3:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 64, 1, 64>, 64, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 32, 2, 64>, 32, 0);
       break;
     default:
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 128, 4, 256>, 128, 0);
