@@ -89,6 +89,14 @@ typedef struct {
                          0: the analytic planner's choice. */
   int32_t ff_shape;   /* -1 (default): chosen as above; 0..3: use that FP32 block shape (see
                          hobi_plan_info) */
+  int32_t fast_degree; /* 0 (default): the FP32 far field is summed directly over every node, as in
+                          the paper. 2..10: fast summation by a barycentric Lagrange treecode of
+                          this interpolation degree (beyond the paper, which names fast summation
+                          as future work; see hobi_fast_info). FP32_BULK precision, HOBI scheme,
+                          single-molecule handles only; the FP64 path stays direct. */
+  double fast_theta;   /* treecode admissibility parameter in (0, 1] (default 0.7): a source
+                          cluster C of more than (n+1)^3 nodes acts on a target batch B through its
+                          (n+1)^3 Chebyshev proxy points when r_B + r_C < theta |c_B - c_C| */
 } hobi_options;
 
 typedef struct {
@@ -211,10 +219,21 @@ int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* 
  * a replayed GMRES graph counts each of its kernels). */
 int hobi_kernel_launches(hobi_t h, int64_t* n);
 
-/* The FP32 far-field launch plan of the matvec: block shape index (0: 256 threads x 4 targets,
- * 256-node tiles; 1: 128 x 4, 128; 2: 128 x 2, 64; 3: 64 x 2, 64), source chunks, and whether
+/* The FP32 far-field launch plan of the matvec: block shape index (0: 128 threads x 8 targets,
+ * 256-node tiles; 1: 64 x 8, 128; 2: 32 x 8, 64; 3: 32 x 4, 64), source chunks, and whether
  * the shape was measured by the autotuner (1) or chosen analytically (0). */
 int hobi_plan_info(hobi_t h, int32_t* shape, int32_t* chunks, int32_t* tuned);
+
+/* Fast summation (options.fast_degree > 0; no counterpart in the paper, which sums the far field
+ * directly and names fast summation as future work). The treecode is planned once in hobi_setup:
+ * an octree over the regular-rule nodes (leaves of at most 256 nodes), target batches of 256
+ * vertices (recursive splits along the longest box axis) and, per batch, the source clusters
+ * summed directly and those replaced by their (n+1)^3 Chebyshev proxy points. Reports, per
+ * matvec, the pair evaluations with nodes (direct_pairs) and with proxy points (approx_pairs),
+ * and the numbers of batches, proxy clusters and evaluation tasks. All zero when fast summation
+ * is off. Any pointer may be NULL. */
+int hobi_fast_info(hobi_t h, int64_t* direct_pairs, int64_t* approx_pairs, int32_t* batches,
+                   int32_t* proxy_clusters, int32_t* tasks);
 
 /* Free every resource of the handle (NULL is a no-op). */
 void hobi_destroy(hobi_t h);

@@ -72,31 +72,47 @@ __device__ __forceinline__ bool tile_wait(unsigned long long* bar, uint32_t pari
   return false;
 }
 
-// One block's share of the FP32 far field: NT threads, 2 TP targets per thread (targets
-// bx*NT*2TP ...), against source tiles [t0, t1) of TILE nodes; results (FP64) to out[i] (row 1)
-// and out[nt + i] (row 2). SKIP_SELF: a pair at zero distance (a collocation point that is also
-// a source node, LOBI-PB) contributes nothing. KS: coordinates and m are stored multiplied by
-// kappa (FF32Consts), so kappa r is the scaled distance itself.
+// Source tiles of the FP32 far field. ContigTiles: tiles [t0, t0 + n) of TILE nodes of one
+// array. SegmentTiles: a list of (first entry, count <= stage capacity) pieces of one array.
+template <int TILE>
+struct ContigTiles {
+  const float4* src;
+  int t0;
+  __device__ __forceinline__ const float4* ptr(int k) const { return src + (size_t)(t0 + k) * (4 * TILE); }
+  __device__ __forceinline__ int count(int) const { return TILE; }
+};
+struct SegmentTiles {
+  const float4* src;
+  const int2* seg;
+  __device__ __forceinline__ const float4* ptr(int k) const { return src + 4 * (size_t)seg[k].x; }
+  __device__ __forceinline__ int count(int k) const { return seg[k].y; }
+};
+
+// One block's FP32 far field: NT threads with 2 TP targets each (targets first + threadIdx.x +
+// k NT, below lim) against `ntile` source tiles of at most TILE nodes; results (FP64) to
+// out[o] (row 1) and out[ld2 + o] (row 2), o = map[i] (or i without a map). SKIP_SELF: a pair at
+// zero distance (a collocation point that is also a source node, LOBI-PB) contributes nothing.
+// KS: coordinates and m are stored multiplied by kappa (FF32Consts), so kappa r is the scaled
+// distance itself.
 // Tiles stream through two shared-memory stages (sh: 2 x 4 TILE float4) by bulk asynchronous
 // copies issued by thread 0, each stage with its mbarrier (bars, initialised by
 // tile_barriers_init); `phases` carries the two barriers' parities across calls of one block.
 // If a barrier wait exceeds its bound, *err is set, in-flight copies are awaited (bounded) and
 // false is returned without writing outputs.
-template <bool ROW2, bool KS, bool SKIP_SELF = false, int NT = kFF32Threads, int TP = kFF32Targets / 2,
-          int TILE = kTile>
-__device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src,
-                                           int t0, int t1, const FF32Consts& cs, double* __restrict__ out, int bx,
-                                           float4* sh, unsigned long long* bars, uint32_t& phases, int* err) {
-  constexpr uint32_t kTileBytes = 4 * TILE * sizeof(float4);
+template <bool ROW2, bool KS, bool SKIP_SELF, int NT, int TP, int TILE, class Tiles>
+__device__ __forceinline__ bool ff32_core(const float4* __restrict__ tgt, int first, int lim,
+                                          const int* __restrict__ map, int ld2, const Tiles& tiles, int ntile,
+                                          const FF32Consts& cs, double* __restrict__ out, float4* sh,
+                                          unsigned long long* bars, uint32_t& phases, int* err) {
   constexpr int T = 2 * TP;
   constexpr int kUnroll = TP >= 4 ? 1 : 2;  // 4 packed pairs already give enough independent chains
   float2 px[TP], py[TP], pz[TP];  // target k = 2p + lane
   float qx[T], qy[T], qz[T];
   float h1[T], l1[T], h2[T], l2[T];
-  const int base = bx * (NT * T) + threadIdx.x;
+  const int base = first + threadIdx.x;
 #pragma unroll
   for (int k = 0; k < T; ++k) {
-    int i = min(base + k * NT, nt - 1);
+    int i = min(base + k * NT, lim - 1);
     float4 a = tgt[2 * (size_t)i], b = tgt[2 * (size_t)i + 1];
     if (k & 1) {
       px[k >> 1].y = a.x; py[k >> 1].y = a.y; pz[k >> 1].y = a.z;
@@ -111,11 +127,10 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
   const float2 l2e = pair_of(kLog2e), nl2e = pair_of(-kLog2e);
   const float2 kap2 = pair_of(cs.kap), nk2 = pair_of(cs.neg_kl2e), kk2 = pair_of(cs.kap_sq);
   const float2 omie = pair_of(cs.one_minus_inv_eps);
-  const int ntile = t1 - t0;
   __syncthreads();  // the stages are free (a previous call of this block has consumed them)
   if (threadIdx.x == 0)
     for (int k = 0; k < 2 && k < ntile; ++k)
-      tile_copy(sh + k * 4 * TILE, src + (size_t)(t0 + k) * (4 * TILE), kTileBytes, &bars[k]);
+      tile_copy(sh + k * 4 * TILE, tiles.ptr(k), (uint32_t)tiles.count(k) * 4 * sizeof(float4), &bars[k]);
   for (int kt = 0; kt < ntile; ++kt) {  // kt: tile of this call
     const int stage = kt & 1;
     const bool ok = tile_wait(&bars[stage], (phases >> stage) & 1u);
@@ -128,11 +143,12 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
     }
     phases ^= 1u << stage;
     const float4* cur = sh + stage * 4 * TILE;
+    const int cnt = tiles.count(kt);
     float2 a1[TP], wx[TP], wy[TP], wz[TP];
 #pragma unroll
     for (int k = 0; k < TP; ++k) a1[k] = wx[k] = wy[k] = wz[k] = pair_of(0.f);
 #pragma unroll kUnroll
-    for (int s = 0; s < TILE; ++s) {
+    for (int s = 0; s < cnt; ++s) {
       const float4 A = cur[4 * s], B = cur[4 * s + 1], C = cur[4 * s + 2], D = cur[4 * s + 3];
       const float2 nyx = make_float2(A.x, A.y), nyy = make_float2(A.z, A.w), nyz = make_float2(B.x, B.y);
       const float2 se = make_float2(B.z, B.w), mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w);
@@ -190,17 +206,31 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
     }
     __syncthreads();  // every thread has finished reading this stage
     if (threadIdx.x == 0 && kt + 2 < ntile)
-      tile_copy(sh + stage * 4 * TILE, src + (size_t)(t0 + kt + 2) * (4 * TILE), kTileBytes, &bars[stage]);
+      tile_copy(sh + stage * 4 * TILE, tiles.ptr(kt + 2), (uint32_t)tiles.count(kt + 2) * 4 * sizeof(float4),
+                &bars[stage]);
   }
 #pragma unroll
   for (int k = 0; k < T; ++k) {
-    int i = base + k * NT;
-    if (i < nt) {
-      out[i] = ((double)h1[k] + (double)l1[k]) * cs.row1_scale;
-      if (ROW2) out[nt + i] = ((double)h2[k] + (double)l2[k]) * cs.row2_scale;
+    const int i = base + k * NT;
+    if (i < lim) {
+      const int o = map ? map[i] : i;
+      out[o] = ((double)h1[k] + (double)l1[k]) * cs.row1_scale;
+      if (ROW2) out[ld2 + o] = ((double)h2[k] + (double)l2[k]) * cs.row2_scale;
     }
   }
   return true;
+}
+
+// One block's share of the FP32 far field over contiguous tiles: targets bx*NT*2TP ... of nt,
+// source tiles [t0, t1) of TILE nodes, rows to out[i] and out[nt + i] (see ff32_core).
+template <bool ROW2, bool KS, bool SKIP_SELF = false, int NT = kFF32Threads, int TP = kFF32Targets / 2,
+          int TILE = kTile>
+__device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int nt, const float4* __restrict__ src,
+                                           int t0, int t1, const FF32Consts& cs, double* __restrict__ out, int bx,
+                                           float4* sh, unsigned long long* bars, uint32_t& phases, int* err) {
+  const ContigTiles<TILE> tiles{src, t0};
+  return ff32_core<ROW2, KS, SKIP_SELF, NT, TP, TILE>(tgt, bx * (NT * 2 * TP), nt, nullptr, nt, tiles, t1 - t0, cs,
+                                                       out, sh, bars, phases, err);
 }
 
 // One block's share of the FP64 far field (2 targets per thread); sh: 4 kTile double2.
@@ -266,7 +296,7 @@ __device__ __forceinline__ void gather32_node(int node, int nv, const int* __res
                                               const double* __restrict__ ny, const double* __restrict__ nnu,
                                               const double* __restrict__ nW, const double* __restrict__ center,
                                               const double* __restrict__ u, double inv_eps, double xs,
-                                              float4* __restrict__ src) {
+                                              float4* __restrict__ src, int slot) {
   int j = node >> 2;
   int a = F[3 * j], b = F[3 * j + 1], c = F[3 * j + 2];
   const double* W = nW + 3 * (size_t)node;
@@ -279,7 +309,7 @@ __device__ __forceinline__ void gather32_node(int node, int nv, const int* __res
   const float se = (float)(sig * inv_eps), sd = (float)(sig * inv_eps - sig);
   const double xm = xs * mu;
   const float mx = (float)(xm * n[0]), my = (float)(xm * n[1]), mz = (float)(xm * n[2]);
-  float4* o = src + 4 * (size_t)node;
+  float4* o = src + 4 * (size_t)slot;
   o[0] = make_float4(yx, yx, yy, yy);
   o[1] = make_float4(yz, yz, se, se);
   o[2] = make_float4(mx, mx, my, my);

@@ -68,6 +68,17 @@ struct hobi_ctx {
   double eps1 = 1, eps2 = 80, kappa = 0, eps = 80;
   double xs = 1;            // coordinate scale of the FP32 tables (ff32_coord_scale(kappa))
   int num_sms = 1;
+  // fast summation (treecode) of the FP32 far field; fast_degree 0: direct summation
+  int fast_degree = 0, fast_chunks = 1, fast_ntasks = 0, fast_nup = 0, fast_npc = 0, fast_grid = 1;
+  int fast_batches = 0, fast_nseg = 0;
+  double fast_theta = 0.7;
+  int64_t fast_direct_pairs = 0, fast_approx_pairs = 0;
+  int *fast_pos = nullptr, *fast_tmap = nullptr, *fast_pcoff = nullptr, *fast_counter = nullptr;
+  int2 *fast_batch = nullptr, *fast_seg = nullptr, *fast_pcitems = nullptr;
+  FastTask* fast_tasks = nullptr;
+  FastUpItem* fast_up = nullptr;
+  float *fast_axes = nullptr, *fast_half = nullptr;
+  float4 *fast_src = nullptr, *fast_tgt = nullptr, *fast_partial = nullptr;
   std::vector<void*> allocs;
   // inputs and geometry
   double *V = nullptr, *Nin = nullptr, *Nv = nullptr, *Q = nullptr;
@@ -175,17 +186,33 @@ struct hobi_ctx {
   }
 
   // --------------------------------------------------------------- matvec pipeline
+  bool fast_active(bool fp32) const { return fp32 && fast_degree > 0; }
+  // one far-field evaluation: the planned direct kernel, or (fast) the treecode's proxy densities
+  // and its list evaluation into the fast_chunks partial rows
+  int launch_ff(bool fp32, bool fast, const FarFieldPlan& p, const float4* t32, const double* t64, double* out,
+                bool skip_self) {
+    if (!fast) {
+      HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, ff_err, stream, skip_self));
+      return HOBI_OK;
+    }
+    HOBI_CK(launch_fast_upward(fast_nup, fast_up, fast_axes, fast_half, fast_src, fast_degree, fast_partial, fast_npc,
+                               fast_pcitems, fast_pcoff, eps, stream));
+    HOBI_CK(launch_fast_eval(fast_tasks, fast_ntasks, fast_counter, fast_batch, fast_seg, fast_src, fast_tgt,
+                             fast_tmap, (int)nv, eps, kappa, out, fast_grid, ff_err, stream));
+    return HOBI_OK;
+  }
   int farfield(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, double* out,
-               bool skip_self = false) {
+               bool skip_self = false, bool fast = false) {
+    const double pairs = fast ? (double)(fast_direct_pairs + fast_approx_pairs) : (double)p.n_targets * (double)n_nodes;
     cudaEvent_t a = nullptr, bb = nullptr;
     if (prof && capturing) {
       const int pi = fp32 ? 1 : 0;
       for (int q = 0; q < 2; ++q)
         if (!gev[pi][q]) HOBI_CK(cudaEventCreate(&gev[pi][q]));
       HOBI_CK(cudaEventRecordWithFlags(gev[pi][0], stream, cudaEventRecordExternal));
-      HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, ff_err, stream, skip_self));
+      HOBI_TRY(launch_ff(fp32, fast, p, t32, t64, out, skip_self));
       HOBI_CK(cudaEventRecordWithFlags(gev[pi][1], stream, cudaEventRecordExternal));
-      graph_pairs[pi] = (double)p.n_targets * (double)n_nodes;
+      graph_pairs[pi] = pairs;
       return HOBI_OK;
     }
     if (prof) {
@@ -200,22 +227,71 @@ struct hobi_ctx {
       ++prof_used;
       HOBI_CK(cudaEventRecord(a, stream));
     }
-    HOBI_CK(launch_farfield(fp32, p, t32, t64, src32, src64, eps, kappa, out, ff_err, stream, skip_self));
+    HOBI_TRY(launch_ff(fp32, fast, p, t32, t64, out, skip_self));
     if (prof) {
       HOBI_CK(cudaEventRecord(bb, stream));
-      pending_pairs += (double)p.n_targets * (double)n_nodes;
+      pending_pairs += pairs;
     }
     return HOBI_OK;
   }
 
   // node densities of u (scheme-dependent node layout)
-  int gather(bool fp32, const double* u, const int* kptr, int64_t ld) {
+  int gather(bool fp32, const double* u, const int* kptr, int64_t ld, bool fast = false) {
     if (scheme == HOBI_SCHEME_LOBI)
       HOBI_CK(launch_gather_lobi(fp32, (int)nf, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps, xs, src32, src64,
                                  stream));
+    else if (fast)  // tree order, into the treecode's source entries
+      HOBI_CK(launch_gather(true, (int)n_nodes, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps, xs,
+                            fast_src, src64, stream, fast_pos));
     else
       HOBI_CK(launch_gather(fp32, (int)n_nodes, (int)nv, F, ny, nnu, nW, center, u, kptr, ld, 1.0 / eps, xs,
                             src32, src64, stream));
+    return HOBI_OK;
+  }
+
+  template <class T>
+  int upload(T** dev, const std::vector<T>& v) {
+    HOBI_TRY(alloc(dev, v.size()));
+    if (!v.empty()) HOBI_CK(cudaMemcpyAsync(*dev, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, stream));
+    return HOBI_OK;
+  }
+  // Treecode plan (host) from the FP64 node and vertex coordinates, uploaded with its buffers.
+  int setup_fast() {
+    std::vector<double> hy(3 * (size_t)n_nodes), hx(3 * (size_t)nv), hc(3);
+    HOBI_CK(cudaMemcpyAsync(hy.data(), ny, sizeof(double) * hy.size(), cudaMemcpyDeviceToHost, stream));
+    HOBI_CK(cudaMemcpyAsync(hx.data(), V, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost, stream));
+    HOBI_CK(cudaMemcpyAsync(hc.data(), center, sizeof(double) * 3, cudaMemcpyDeviceToHost, stream));
+    HOBI_CK(cudaStreamSynchronize(stream));
+    fast_grid = num_sms * fast_eval_blocks_per_sm(kappa);
+    FastPlanHost P;
+    build_fast_plan(hy.data(), (int)n_nodes, hx.data(), (int)nv, hc.data(), xs, fast_degree, fast_theta, fast_grid,
+                    &P);
+    const int n3 = (fast_degree + 1) * (fast_degree + 1) * (fast_degree + 1);
+    fast_chunks = P.chunks;
+    fast_ntasks = (int)P.tasks.size();
+    fast_nup = (int)P.up.size();
+    fast_npc = (int)P.pc_offset.size();
+    fast_batches = (int)P.batch.size();
+    fast_nseg = (int)P.seg.size();
+    fast_direct_pairs = P.direct_pairs;
+    fast_approx_pairs = P.approx_pairs;
+    HOBI_TRY(upload(&fast_pos, P.node_pos));
+    HOBI_TRY(upload(&fast_tmap, P.tmap));
+    HOBI_TRY(upload(&fast_batch, P.batch));
+    HOBI_TRY(upload(&fast_seg, P.seg));
+    HOBI_TRY(upload(&fast_tasks, P.tasks));
+    HOBI_TRY(upload(&fast_up, P.up));
+    HOBI_TRY(upload(&fast_pcitems, P.pc_items));
+    HOBI_TRY(upload(&fast_pcoff, P.pc_offset));
+    HOBI_TRY(upload(&fast_axes, P.axes));
+    HOBI_TRY(upload(&fast_half, P.half));
+    HOBI_TRY(alloc(&fast_src, 4 * (size_t)P.n_entries));
+    HOBI_TRY(alloc(&fast_tgt, 2 * (size_t)nv));
+    HOBI_TRY(alloc(&fast_partial, (size_t)fast_nup * n3));
+    HOBI_TRY(alloc(&fast_counter, 1));
+    HOBI_CK(launch_fast_targets((int)nv, fast_tmap, tgt32, fast_tgt, stream));
+    launches += 1;
+    HOBI_CK(cudaStreamSynchronize(stream));  // the host vectors above are released on return
     return HOBI_OK;
   }
 
@@ -223,11 +299,12 @@ struct hobi_ctx {
   int matvec_dev(const double* u, const int* kptr, int64_t ld, double* Au) {
     const bool fp32 = precision == HOBI_FP32_BULK;
     const bool lobi = scheme == HOBI_SCHEME_LOBI;
-    HOBI_TRY(gather(fp32, u, kptr, ld));
-    HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part, lobi));
-    HOBI_CK(launch_combine((int)nv, plan[fp32].chunks, part, F, lobi ? zero_ptr : inc_ptr, inc_face, corr, eps, u,
-                           kptr, ld, Au, stream));
-    if (!capturing) launches += 3;
+    const bool fast = fast_active(fp32);
+    HOBI_TRY(gather(fp32, u, kptr, ld, fast));
+    HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part, lobi, fast));
+    HOBI_CK(launch_combine((int)nv, fast ? fast_chunks : plan[fp32].chunks, part, F, lobi ? zero_ptr : inc_ptr,
+                           inc_face, corr, eps, u, kptr, ld, Au, stream));
+    if (!capturing) launches += fast ? 5 : 3;
     return HOBI_OK;
   }
 
@@ -289,7 +366,7 @@ struct hobi_ctx {
       }
     }
     HOBI_CK(cudaGraphLaunch(gx, stream));
-    launches += kIterationKernels;
+    launches += kIterationKernels + (fast_active(pi) ? 2 : 0);
     if (prof) {
       replay_prof_pending = true;
       replay_prof_pi = pi;
@@ -557,11 +634,15 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   }
   h->plan[0] = plan_farfield(false, (int)h->nv, (int)h->n_pad, true, h->num_sms, farfield_blocks_per_sm(false, true));
   part_elems = std::max(part_elems, (size_t)h->plan[0].chunks * 2 * h->nv);
+  if (h->fast_degree > 0) {
+    HOBI_TRY(h->setup_fast());
+    part_elems = std::max(part_elems, (size_t)h->fast_chunks * 2 * h->nv);
+  }
   HOBI_TRY(h->alloc(&h->part, part_elems));
   int shape = choose_shape((int)h->nv, (int)h->n_pad, h->num_sms);
   if (h->ff_shape >= 0) {
     shape = h->ff_shape;
-  } else if (h->autotune) {
+  } else if (h->autotune && h->fast_degree == 0) {
     const std::string key = tune_key(h->device, h->scheme, h->nv, h->n_pad);
     if (tune_lookup(key, &shape)) {
       h->tuned = 1;
@@ -633,6 +714,8 @@ void hobi_default_options(hobi_options* opt) {
   opt->scheme = HOBI_SCHEME_HOBI;
   opt->autotune = 1;
   opt->ff_shape = -1;
+  opt->fast_degree = 0;
+  opt->fast_theta = 0.7;
 }
 
 const char* hobi_last_error(void) { return g_err.c_str(); }
@@ -662,6 +745,12 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   if (o.precision != HOBI_FP64 && o.precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
   if (o.scheme != HOBI_SCHEME_HOBI && o.scheme != HOBI_SCHEME_LOBI) return fail(HOBI_ERR_ARG, "unknown scheme");
   if (o.ff_shape < -1 || o.ff_shape >= kNumFF32Shapes) return fail(HOBI_ERR_ARG, "ff_shape must be -1 or 0..3");
+  if (o.fast_degree != 0 && (o.fast_degree < 2 || o.fast_degree > kFastMaxDegree))
+    return fail(HOBI_ERR_ARG, "fast_degree must be 0 (direct far field) or 2..10");
+  if (o.fast_degree != 0 && !(o.fast_theta > 0.0 && o.fast_theta <= 1.0))
+    return fail(HOBI_ERR_ARG, "fast_theta must be in (0, 1]");
+  if (o.fast_degree != 0 && o.scheme != HOBI_SCHEME_HOBI)
+    return fail(HOBI_ERR_ARG, "fast summation is implemented for the HOBI scheme only");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
 
@@ -681,6 +770,8 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   h->scheme = o.scheme;
   h->autotune = o.autotune ? 1 : 0;
   h->ff_shape = o.ff_shape;
+  h->fast_degree = o.fast_degree;
+  h->fast_theta = o.fast_theta;
   h->nv = n_v;
   h->nf = n_f;
   h->nc = n_c;
@@ -987,6 +1078,17 @@ int hobi_plan_info(hobi_t h, int32_t* shape, int32_t* chunks, int32_t* tuned) {
   if (shape) *shape = h->plan[1].shape;
   if (chunks) *chunks = h->plan[1].chunks;
   if (tuned) *tuned = h->tuned;
+  return HOBI_OK;
+}
+
+int hobi_fast_info(hobi_t h, int64_t* direct_pairs, int64_t* approx_pairs, int32_t* batches, int32_t* proxy_clusters,
+                   int32_t* tasks) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (direct_pairs) *direct_pairs = h->fast_direct_pairs;
+  if (approx_pairs) *approx_pairs = h->fast_approx_pairs;
+  if (batches) *batches = h->fast_batches;
+  if (proxy_clusters) *proxy_clusters = h->fast_npc;
+  if (tasks) *tasks = h->fast_ntasks;
   return HOBI_OK;
 }
 
@@ -1441,6 +1543,7 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
   if (opt) o = *opt;
   if (o.precision != HOBI_FP64 && o.precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
   if (o.scheme != HOBI_SCHEME_HOBI) return fail(HOBI_ERR_ARG, "the batch API supports the HOBI scheme only");
+  if (o.fast_degree != 0) return fail(HOBI_ERR_ARG, "the batch API evaluates the far field directly (fast_degree 0)");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
   int dev = o.device;

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace hobi {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -109,7 +111,7 @@ cudaError_t launch_points(int np, const double* P, int stride, const double* cen
 cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
                           const int* kptr, int64_t ld, double inv_eps, double xs, float4* src32, double* src64,
-                          cudaStream_t s);
+                          cudaStream_t s, const int* pos = nullptr);
 cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* src64, cudaStream_t s);
 
 // FP32 far-field block shapes (threads, targets per thread, source tile): 0 = 128 x 8, tile 256;
@@ -216,6 +218,47 @@ constexpr int kTilesPerTask = 16;  // kTile-node tiles per task (FP64), i.e. 409
 constexpr int kBatchFF32Threads = 32;
 constexpr int kBatchFF32Tile = 64;
 constexpr int kBatchFF32TilesPerTask = kTilesPerTask * kTile / kBatchFF32Tile;
+// ---- fast summation of the far field (k_fast.cu): barycentric Lagrange treecode ----
+constexpr int kFastLeaf = 256;      // source-tree leaf size (nodes)
+constexpr int kFastBatch = 256;     // targets per batch = per evaluation block
+constexpr int kFastThreads = 32;    // evaluation block: one warp, 8 targets per thread
+constexpr int kFastSeg = 64;        // source entries per segment (one shared-memory stage)
+constexpr int kFastUpSpan = 2048;   // nodes per upward work item
+constexpr int kFastMaxDegree = 10;
+struct FastTask {                   // one evaluation task: segments [s0, s1) of a batch
+  int batch, s0, s1, chunk;
+};
+struct FastUpItem {                 // nodes [n0, n1) (tree order) of proxy cluster pc
+  int pc, n0, n1;
+};
+struct FastPlanHost {
+  int degree = 0, chunks = 1, n_entries = 0;
+  int64_t direct_pairs = 0, approx_pairs = 0;
+  std::vector<int> node_pos;        // node -> tree position
+  std::vector<int> tmap;            // batch order position -> target
+  std::vector<int2> batch;          // (first position, count)
+  std::vector<int2> seg;            // (source entry, count <= kFastSeg)
+  std::vector<FastTask> tasks;      // longest first
+  std::vector<FastUpItem> up;
+  std::vector<int2> pc_items;       // per proxy cluster: (first item, items)
+  std::vector<int> pc_offset;       // per proxy cluster: first proxy entry
+  std::vector<int> pc_cluster;      // per proxy cluster: source-tree cluster
+  std::vector<float> axes;          // per proxy cluster: 3 x (n+1) scaled Chebyshev coordinates
+  std::vector<float> half;          // per proxy cluster: 3 scaled half-extents
+};
+// y: nodes (n_nodes x 3), x: targets (nv x 3), FP64 absolute coordinates; center and xs as for
+// the FP32 tables. resident_blocks sizes the task split.
+int build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const double* center, double xs,
+                    int degree, double theta, int resident_blocks, FastPlanHost* out);
+cudaError_t launch_fast_targets(int nv, const int* tmap, const float4* tgt32, float4* tgtf, cudaStream_t s);
+cudaError_t launch_fast_upward(int nup, const FastUpItem* items, const float* axes, const float* half,
+                               float4* srcf, int degree, float4* partial, int npc, const int2* pc_items,
+                               const int* pc_off, double eps, cudaStream_t s);
+cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, int* counter, const int2* batch, const int2* seg,
+                             const float4* srcf, const float4* tgtf, const int* tmap, int nv, double eps,
+                             double kappa, double* part, int grid, int* err, cudaStream_t s);
+int fast_eval_blocks_per_sm(double kappa);
+
 cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const int64_t* node_off, int64_t total_nodes,
                                 const double* u, const int* kptr, int64_t ld, const MolState* ms, cudaStream_t s);
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,

@@ -59,7 +59,7 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
   const double* um = u + (kptr ? (int64_t)(*kptr) * ld : 0) + d.u_off;
   int node = (int)(g - node_off[m]);
   if (fp32)
-    ff::gather32_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.xs, d.src32);
+    ff::gather32_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.xs, d.src32, node);
   else
     ff::gather64_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, d.src64);
 }

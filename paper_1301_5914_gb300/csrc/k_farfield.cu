@@ -41,11 +41,12 @@ namespace {
 __global__ void k_gather32(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
                            const double* __restrict__ nnu, const double* __restrict__ nW,
                            const double* __restrict__ center, const double* __restrict__ u, const int* kptr,
-                           int64_t ld, double inv_eps, double xs, float4* __restrict__ src) {
+                           int64_t ld, double inv_eps, double xs, float4* __restrict__ src,
+                           const int* __restrict__ pos) {
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= n_nodes) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
-  ff::gather32_node(node, nv, F, ny, nnu, nW, center, u, inv_eps, xs, src);
+  ff::gather32_node(node, nv, F, ny, nnu, nW, center, u, inv_eps, xs, src, pos ? pos[node] : node);
 }
 
 __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
@@ -157,10 +158,10 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const double* ny,
                           const double* nnu, const double* nW, const double* center, const double* u,
                           const int* kptr, int64_t ld, double inv_eps, double xs, float4* src32, double* src64,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int* pos) {
   if (fp32)
     k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, xs,
-                                                  src32);
+                                                  src32, pos);
   else
     k_gather64<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, src64);
   return cudaGetLastError();

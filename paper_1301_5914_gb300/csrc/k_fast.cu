@@ -1,0 +1,440 @@
+// k_fast.cu -- fast summation of the far field: a barycentric Lagrange treecode (beyond the
+// paper, which evaluates the far field directly and names fast summation as future work; the
+// method is Wang, Tlupova and Krasny's kernel-independent treecode, 2020).
+//
+// The far-field sum of a matvec (the regular-rule part of Eqs. eqdbef3-eqdbef4) is linear in
+// the node densities sigma and m with coefficients that are smooth functions of the source
+// position away from the target. For a target batch B and a source cluster C that are well
+// separated, the sum over C's nodes is replaced by a sum over C's (n+1)^3 tensor Chebyshev
+// points (second kind, in C's bounding box) whose densities are the nodes' densities
+// interpolated onto them with the barycentric Lagrange basis. Because the pair formula is the
+// same, the proxies are simply more source entries in the FP32 source layout, and the
+// evaluation kernel is the far-field block of ff_body.cuh run over a list of source segments.
+//
+// Setup (host): an octree over the nodes (tight boxes, midpoint octants, leaves of at most
+// kFastLeaf nodes, depth-first order), target batches by recursive longest-axis splits into sets
+// of kFastBatch targets, and per batch the traversal: a cluster of more than (n+1)^3 nodes with
+// r_B + r_C < theta |c_B - c_C| is approximated, a leaf otherwise summed directly, an inner
+// cluster opened. Each batch's segment list is cut into `chunks` pieces of equal work.
+// Per matvec: the gather writes the node densities in tree order, the upward kernels form the
+// proxy densities, and a persistent kernel evaluates (batch, piece) tasks into per-piece partial
+// rows, which the usual combine kernel adds up with the singular correction.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ff_body.cuh"
+
+namespace hobi {
+
+// ------------------------------------------------------------------ host: plan construction
+namespace {
+
+struct Cluster {
+  int begin, end;
+  double lo[3], hi[3];
+  std::vector<int> children;
+};
+
+void tight_box(const double* P, const int* idx, int n, double* lo, double* hi) {
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = P[3 * (size_t)idx[0] + d];
+    hi[d] = lo[d];
+  }
+  for (int t = 1; t < n; ++t)
+    for (int d = 0; d < 3; ++d) {
+      const double v = P[3 * (size_t)idx[t] + d];
+      lo[d] = std::min(lo[d], v);
+      hi[d] = std::max(hi[d], v);
+    }
+}
+
+// Octree over the points: tight boxes, a cluster of more than `leaf` points whose box is not a
+// point splits into the octants of its box midpoint (coordinate > midpoint is the upper half,
+// octant index x + 2y + 4z, empty octants dropped); points listed depth first.
+int build_octree(const double* P, std::vector<int>& idx, int leaf, std::vector<Cluster>& cl, std::vector<int>& order) {
+  const int ci = (int)cl.size();
+  cl.push_back(Cluster());
+  cl[ci].begin = (int)order.size();
+  double lo[3], hi[3];
+  tight_box(P, idx.data(), (int)idx.size(), lo, hi);
+  std::memcpy(cl[ci].lo, lo, sizeof lo);
+  std::memcpy(cl[ci].hi, hi, sizeof hi);
+  const bool flat = !(hi[0] > lo[0] || hi[1] > lo[1] || hi[2] > lo[2]);
+  if ((int)idx.size() > leaf && !flat) {
+    const double mid[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
+    std::vector<int> oct[8];
+    for (int t : idx) {
+      const double* p = P + 3 * (size_t)t;
+      oct[(p[0] > mid[0] ? 1 : 0) + (p[1] > mid[1] ? 2 : 0) + (p[2] > mid[2] ? 4 : 0)].push_back(t);
+    }
+    std::vector<int>().swap(idx);
+    for (int o = 0; o < 8; ++o)
+      if (!oct[o].empty()) {
+        const int ch = build_octree(P, oct[o], leaf, cl, order);
+        cl[ci].children.push_back(ch);
+      }
+  } else {
+    order.insert(order.end(), idx.begin(), idx.end());
+  }
+  cl[ci].end = (int)order.size();
+  return ci;
+}
+
+// Target batches: a set of c > batch targets is ordered along the longest axis of its tight box
+// (ties by index) and split after floor(ceil(c / batch) / 2) * batch targets.
+void build_batches(const double* X, std::vector<int>& idx, int batch, std::vector<Cluster>& out,
+                   std::vector<int>& order) {
+  double lo[3], hi[3];
+  tight_box(X, idx.data(), (int)idx.size(), lo, hi);
+  const int c = (int)idx.size();
+  if (c <= batch) {
+    Cluster b;
+    b.begin = (int)order.size();
+    b.end = b.begin + c;
+    std::memcpy(b.lo, lo, sizeof lo);
+    std::memcpy(b.hi, hi, sizeof hi);
+    out.push_back(b);
+    order.insert(order.end(), idx.begin(), idx.end());
+    return;
+  }
+  int a = 0;
+  for (int d = 1; d < 3; ++d)
+    if (hi[d] - lo[d] > hi[a] - lo[a]) a = d;
+  std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) {
+    const double vp = X[3 * (size_t)p + a], vq = X[3 * (size_t)q + a];
+    return vp < vq || (vp == vq && p < q);
+  });
+  const int cut = (c + batch - 1) / batch / 2 * batch;
+  std::vector<int> left(idx.begin(), idx.begin() + cut), right(idx.begin() + cut, idx.end());
+  std::vector<int>().swap(idx);
+  build_batches(X, left, batch, out, order);
+  build_batches(X, right, batch, out, order);
+}
+
+void center_radius(const Cluster& c, double* ctr, double* r) {
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    ctr[d] = 0.5 * (c.lo[d] + c.hi[d]);
+    const double e = c.hi[d] - c.lo[d];
+    s += e * e;
+  }
+  *r = 0.5 * std::sqrt(s);
+}
+
+void traverse(const std::vector<Cluster>& cl, int ci, const double* cb, double rb, double theta, int n3,
+              std::vector<int>& direct, std::vector<int>& approx) {
+  const Cluster& c = cl[ci];
+  double cc[3], rc;
+  center_radius(c, cc, &rc);
+  const double dx = cc[0] - cb[0], dy = cc[1] - cb[1], dz = cc[2] - cb[2];
+  if (c.end - c.begin > n3 && rb + rc < theta * std::sqrt(dx * dx + dy * dy + dz * dz)) {
+    approx.push_back(ci);
+  } else if (c.children.empty()) {
+    direct.push_back(ci);
+  } else {
+    for (int ch : c.children) traverse(cl, ch, cb, rb, theta, n3, direct, approx);
+  }
+}
+
+}  // namespace
+
+int build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const double* center, double xs,
+                    int degree, double theta, int resident_blocks, FastPlanHost* out) {
+  FastPlanHost& F = *out;
+  F = FastPlanHost();
+  const int n1 = degree + 1, n3 = n1 * n1 * n1;
+  F.degree = degree;
+  // source tree
+  std::vector<Cluster> cl;
+  std::vector<int> order, idx(n_nodes);
+  for (int t = 0; t < n_nodes; ++t) idx[t] = t;
+  build_octree(y, idx, kFastLeaf, cl, order);
+  F.node_pos.assign(n_nodes, 0);
+  for (int p = 0; p < n_nodes; ++p) F.node_pos[order[p]] = p;
+  // target batches
+  std::vector<Cluster> bt;
+  std::vector<int> torder, tidx(nv);
+  for (int t = 0; t < nv; ++t) tidx[t] = t;
+  build_batches(x, tidx, kFastBatch, bt, torder);
+  F.tmap = torder;
+  // interaction lists and segments
+  std::vector<int> pc_of(cl.size(), -1);
+  std::vector<std::vector<int2>> segs(bt.size());
+  F.direct_pairs = F.approx_pairs = 0;
+  for (size_t b = 0; b < bt.size(); ++b) {
+    double cb[3], rb;
+    center_radius(bt[b], cb, &rb);
+    std::vector<int> direct, approx;
+    traverse(cl, 0, cb, rb, theta, n3, direct, approx);
+    const int64_t nb = bt[b].end - bt[b].begin;
+    for (int ci : direct) {
+      for (int s = cl[ci].begin; s < cl[ci].end; s += kFastSeg) segs[b].push_back({s, std::min(kFastSeg, cl[ci].end - s)});
+      F.direct_pairs += nb * (cl[ci].end - cl[ci].begin);
+    }
+    for (int ci : approx) {
+      if (pc_of[ci] < 0) {
+        pc_of[ci] = (int)F.pc_offset.size();
+        F.pc_offset.push_back(n_nodes + n3 * (int)(F.pc_offset.size()));
+        F.pc_cluster.push_back(ci);
+      }
+      const int off = F.pc_offset[pc_of[ci]];
+      for (int s = 0; s < n3; s += kFastSeg) segs[b].push_back({off + s, std::min(kFastSeg, n3 - s)});
+      F.approx_pairs += nb * n3;
+    }
+  }
+  const int npc = (int)F.pc_offset.size();
+  F.n_entries = n_nodes + npc * n3;
+  // proxy clusters: Chebyshev axes (scaled, relative to the centroid) and upward work items
+  F.axes.assign((size_t)npc * 3 * n1, 0.f);
+  F.half.assign((size_t)npc * 3, 0.f);
+  for (int pc = 0; pc < npc; ++pc) {
+    const Cluster& c = cl[F.pc_cluster[pc]];
+    double half[3], hmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      half[d] = 0.5 * (c.hi[d] - c.lo[d]);
+      hmax = std::max(hmax, half[d]);
+    }
+    for (int d = 0; d < 3; ++d) {
+      half[d] = std::max(half[d], 1e-3 * hmax);
+      const double mid = 0.5 * (c.lo[d] + c.hi[d]);
+      for (int k = 0; k < n1; ++k)
+        F.axes[((size_t)pc * 3 + d) * n1 + k] =
+            (float)(xs * (mid + half[d] * std::cos(3.14159265358979323846 * k / degree) - center[d]));
+      F.half[(size_t)pc * 3 + d] = (float)(xs * half[d]);
+    }
+    const int first = (int)F.up.size();
+    for (int s = c.begin; s < c.end; s += kFastUpSpan) F.up.push_back({pc, s, std::min(c.end, s + kFastUpSpan)});
+    F.pc_items.push_back({first, (int)F.up.size() - first});
+  }
+  // batches and tasks: every batch's segment list cut into `chunks` pieces of equal work
+  const int nb = (int)bt.size();
+  int chunks = (8 * resident_blocks + nb - 1) / nb;
+  chunks = std::max(1, std::min(chunks, 256));
+  F.chunks = chunks;
+  std::vector<std::pair<int64_t, FastTask>> tl;
+  for (int b = 0; b < nb; ++b) {
+    F.batch.push_back({bt[b].begin, bt[b].end - bt[b].begin});
+    const int s_first = (int)F.seg.size();
+    int64_t total = 0;
+    for (const int2& sg : segs[b]) total += sg.y;
+    F.seg.insert(F.seg.end(), segs[b].begin(), segs[b].end());
+    int64_t acc = 0;
+    int s = 0;
+    const int ns = (int)segs[b].size();
+    for (int c = 0; c < chunks; ++c) {
+      const int s0 = s;
+      const int64_t goal = total * (c + 1) / chunks;
+      while (s < ns && (acc < goal || c == chunks - 1)) acc += segs[b][s++].y;
+      int64_t cost = 0;
+      for (int q = s0; q < s; ++q) cost += segs[b][q].y;
+      tl.push_back({cost, FastTask{b, s_first + s0, s_first + s, c}});
+    }
+  }
+  std::stable_sort(tl.begin(), tl.end(), [](const std::pair<int64_t, FastTask>& a,
+                                             const std::pair<int64_t, FastTask>& b2) { return a.first > b2.first; });
+  for (auto& t : tl) F.tasks.push_back(t.second);
+  return 0;
+}
+
+// ------------------------------------------------------------------ device
+namespace {
+
+// Barycentric Lagrange basis of the Chebyshev points s[0..n1) (weights (-1)^k, halved at both
+// ends) at x; a coordinate within 1e-6 half-extents of a point takes the Kronecker value.
+__device__ __forceinline__ void lagrange_row(float x, const float* s, float h, int n1, float* L) {
+  int hit = -1;
+  for (int k = 0; k < n1; ++k)
+    if (hit < 0 && fabsf(x - s[k]) < 1e-6f * h) hit = k;
+  if (hit >= 0) {
+    for (int k = 0; k < n1; ++k) L[k] = k == hit ? 1.f : 0.f;
+    return;
+  }
+  float den = 0.f;
+  for (int k = 0; k < n1; ++k) {
+    float w = (k & 1) ? -1.f : 1.f;
+    if (k == 0 || k == n1 - 1) w *= 0.5f;
+    const float t = w / (x - s[k]);
+    L[k] = t;
+    den += t;
+  }
+  const float inv = 1.f / den;
+  for (int k = 0; k < n1; ++k) L[k] *= inv;
+}
+
+__global__ void k_fast_targets(int nv, const int* __restrict__ tmap, const float4* __restrict__ tgt32,
+                               float4* __restrict__ tgtf) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nv) return;
+  const int i = tmap[p];
+  tgtf[2 * (size_t)p] = tgt32[2 * (size_t)i];
+  tgtf[2 * (size_t)p + 1] = tgt32[2 * (size_t)i + 1];
+}
+
+constexpr int kUpThreads = 128;
+constexpr int kMaxN1 = kFastMaxDegree + 1;
+constexpr int kUpPer = (kMaxN1 * kMaxN1 * kMaxN1 + kUpThreads - 1) / kUpThreads;
+
+// Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n1) of a proxy cluster.
+__global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __restrict__ items,
+                                                            const float* __restrict__ axes,
+                                                            const float* __restrict__ half,
+                                                            const float4* __restrict__ srcf, int n1,
+                                                            float4* __restrict__ partial) {
+  __shared__ float sL[3][kUpThreads][kMaxN1];
+  __shared__ float4 sq[kUpThreads];
+  const FastUpItem it = items[blockIdx.x];
+  const float* ax = axes + (size_t)it.pc * 3 * n1;
+  const float* hf = half + (size_t)it.pc * 3;
+  const int n3 = n1 * n1 * n1;
+  float4 acc[kUpPer];
+  int pi[kUpPer], pj[kUpPer], pk[kUpPer];
+#pragma unroll
+  for (int q = 0; q < kUpPer; ++q) {
+    acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int p = threadIdx.x + q * kUpThreads;
+    pi[q] = p / (n1 * n1);
+    pj[q] = (p / n1) % n1;
+    pk[q] = p % n1;
+  }
+  for (int c0 = it.n0; c0 < it.n1; c0 += kUpThreads) {
+    const int node = c0 + threadIdx.x;
+    if (node < it.n1) {
+      const float4 A = srcf[4 * (size_t)node], B = srcf[4 * (size_t)node + 1];
+      const float4 C = srcf[4 * (size_t)node + 2], D = srcf[4 * (size_t)node + 3];
+      lagrange_row(-A.x, ax, hf[0], n1, sL[0][threadIdx.x]);
+      lagrange_row(-A.z, ax + n1, hf[1], n1, sL[1][threadIdx.x]);
+      lagrange_row(-B.x, ax + 2 * n1, hf[2], n1, sL[2][threadIdx.x]);
+      sq[threadIdx.x] = make_float4(B.z, C.x, C.z, D.x);  // sigma/eps, m
+    } else {
+      for (int k = 0; k < n1; ++k) sL[0][threadIdx.x][k] = sL[1][threadIdx.x][k] = sL[2][threadIdx.x][k] = 0.f;
+      sq[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int cnt = min(kUpThreads, it.n1 - c0);
+    for (int t = 0; t < cnt; ++t) {
+      const float4 q4 = sq[t];
+#pragma unroll
+      for (int q = 0; q < kUpPer; ++q) {
+        if (threadIdx.x + q * kUpThreads < n3) {
+          const float w = sL[0][t][pi[q]] * sL[1][t][pj[q]] * sL[2][t][pk[q]];
+          acc[q].x = fmaf(w, q4.x, acc[q].x);
+          acc[q].y = fmaf(w, q4.y, acc[q].y);
+          acc[q].z = fmaf(w, q4.z, acc[q].z);
+          acc[q].w = fmaf(w, q4.w, acc[q].w);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kUpPer; ++q) {
+    const int p = threadIdx.x + q * kUpThreads;
+    if (p < n3) partial[(size_t)blockIdx.x * n3 + p] = acc[q];
+  }
+}
+
+// Proxy source entries: partial densities of each cluster's items added in order, written in
+// the FP32 source layout {-s, sigma/eps, m, sigma/eps - sigma} after the tree-ordered nodes.
+__global__ void k_fast_finish(int npc, const int2* __restrict__ pc_items, const int* __restrict__ pc_off,
+                              const float* __restrict__ axes, const float4* __restrict__ partial, int n1,
+                              float one_minus_eps, float4* __restrict__ srcf) {
+  const int n3 = n1 * n1 * n1;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)npc * n3) return;
+  const int pc = (int)(g / n3), p = (int)(g % n3);
+  const int2 r = pc_items[pc];
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = 0; q < r.y; ++q) {
+    const float4 v = partial[(size_t)(r.x + q) * n3 + p];
+    s.x += v.x;
+    s.y += v.y;
+    s.z += v.z;
+    s.w += v.w;
+  }
+  const float* ax = axes + (size_t)pc * 3 * n1;
+  const float x = ax[p / (n1 * n1)], y = ax[n1 + (p / n1) % n1], z = ax[2 * n1 + p % n1];
+  const float sd = s.x * one_minus_eps;
+  float4* o = srcf + 4 * ((size_t)pc_off[pc] + p);
+  o[0] = make_float4(-x, -x, -y, -y);
+  o[1] = make_float4(-z, -z, s.x, s.x);
+  o[2] = make_float4(s.y, s.y, s.z, s.z);
+  o[3] = make_float4(s.w, s.w, sd, sd);
+}
+
+// Persistent evaluation: one-warp blocks pull (batch, piece) tasks from an atomic counter and
+// run the far-field block over the piece's segments into the piece's partial rows.
+template <bool KS>
+__global__ void __launch_bounds__(kFastThreads, 8)
+    k_fast_eval(const FastTask* __restrict__ tasks, int ntasks, int* counter, const int2* __restrict__ batch,
+                const int2* __restrict__ seg, const float4* __restrict__ srcf, const float4* __restrict__ tgtf,
+                const int* __restrict__ tmap, int nv, FF32Consts cs, double* __restrict__ part, int* err) {
+  __shared__ __align__(128) float4 sh[2 * 4 * kFastSeg];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ int s_task;
+  if (threadIdx.x == 0) ff::tile_barriers_init(bars);
+  __syncthreads();
+  uint32_t phases = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= ntasks) break;
+    const FastTask tk = tasks[t];
+    const int2 b = batch[tk.batch];
+    const ff::SegmentTiles tiles{srcf, seg + tk.s0};
+    const bool ok = ff::ff32_core<true, KS, false, kFastThreads, kFF32Targets / 2, kFastSeg>(
+        tgtf, b.x, b.x + b.y, tmap, nv, tiles, tk.s1 - tk.s0, cs, part + (size_t)tk.chunk * 2 * nv, sh, bars,
+        phases, err);
+    if (!ok) return;  // the tile pipeline timed out (reported through err)
+  }
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_fast_targets(int nv, const int* tmap, const float4* tgt32, float4* tgtf, cudaStream_t s) {
+  k_fast_targets<<<nblk(nv, 256), 256, 0, s>>>(nv, tmap, tgt32, tgtf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fast_upward(int nup, const FastUpItem* items, const float* axes, const float* half,
+                               float4* srcf, int degree, float4* partial, int npc, const int2* pc_items,
+                               const int* pc_off, double eps, cudaStream_t s) {
+  const int n1 = degree + 1;
+  if (nup > 0) k_fast_upward<<<nup, kUpThreads, 0, s>>>(items, axes, half, srcf, n1, partial);
+  const int64_t n = (int64_t)npc * n1 * n1 * n1;
+  if (n > 0)
+    k_fast_finish<<<nblk(n, 256), 256, 0, s>>>(npc, pc_items, pc_off, axes, partial, n1, (float)(1.0 - eps), srcf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, int* counter, const int2* batch, const int2* seg,
+                             const float4* srcf, const float4* tgtf, const int* tmap, int nv, double eps,
+                             double kappa, double* part, int grid, int* err, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const FF32Consts cs = ff32_consts(eps, kappa);
+  if (ff32_kappa_scaled(kappa))
+    k_fast_eval<true><<<grid, kFastThreads, 0, s>>>(tasks, ntasks, counter, batch, seg, srcf, tgtf, tmap, nv, cs,
+                                                     part, err);
+  else
+    k_fast_eval<false><<<grid, kFastThreads, 0, s>>>(tasks, ntasks, counter, batch, seg, srcf, tgtf, tmap, nv, cs,
+                                                      part, err);
+  return cudaGetLastError();
+}
+
+int fast_eval_blocks_per_sm(double kappa) {
+  int n = 1;
+  if (ff32_kappa_scaled(kappa))
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_eval<true>, kFastThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_eval<false>, kFastThreads, 0);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace hobi

@@ -37,6 +37,7 @@ EXPORTS = [
     "hobi_solve", "hobi_solve_from", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
     "hobi_reaction_potential_noalloc", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
+    "hobi_fast_info",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
     "hobi_matvec_batch", "hobi_solve_batch", "hobi_energy_batch", "hobi_batch_kernel_launches", "hobi_destroy_batch",
     "hobi_batch_profile_enable", "hobi_batch_profile_read",
@@ -52,7 +53,8 @@ class HobiError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mem_device", C.c_int32), ("stream", C.c_void_p),
                 ("restart", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32), ("scheme", C.c_int32),
-                ("autotune", C.c_int32), ("ff_shape", C.c_int32)]
+                ("autotune", C.c_int32), ("ff_shape", C.c_int32), ("fast_degree", C.c_int32),
+                ("fast_theta", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -141,7 +143,8 @@ class Solver:
 
     def __init__(self, V, F, N, charges, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
                  restart: int = 50, use_graph: bool = True, device: int | None = None, stream=None,
-                 scheme: str = "hobi", autotune: bool = True, ff_shape: int = -1):
+                 scheme: str = "hobi", autotune: bool = True, ff_shape: int = -1, fast_degree: int = 0,
+                 fast_theta: float = 0.7):
         lib = load_library()
         self._lib = lib
         self.device_mode = _is_cuda_tensor(V)
@@ -153,6 +156,8 @@ class Solver:
         opt.scheme = HOBI_SCHEME_LOBI if scheme == "lobi" else HOBI_SCHEME_HOBI
         opt.autotune = 1 if autotune else 0
         opt.ff_shape = int(ff_shape)
+        opt.fast_degree = int(fast_degree)
+        opt.fast_theta = float(fast_theta)
         if self.device_mode:
             import torch
 
@@ -323,6 +328,14 @@ class Solver:
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         _check(self._lib.hobi_plan_info(self._h, C.byref(a), C.byref(b), C.byref(c)))
         return {"shape": a.value, "chunks": b.value, "tuned": bool(c.value)}
+
+    def fast_info(self):
+        """Treecode statistics per matvec (all zero when fast summation is off)."""
+        d, a = C.c_int64(), C.c_int64()
+        b, p, t = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._lib.hobi_fast_info(self._h, C.byref(d), C.byref(a), C.byref(b), C.byref(p), C.byref(t)))
+        return {"direct_pairs": d.value, "approx_pairs": a.value, "batches": b.value, "proxy_clusters": p.value,
+                "tasks": t.value}
 
     def profile_enable(self, on: bool = True):
         _check(self._lib.hobi_profile_enable(self._h, 1 if on else 0))

@@ -1,0 +1,113 @@
+"""Fast summation (treecode) of the FP32 far field against the oracle.
+
+The CUDA treecode must give the oracle treecode's operator (same tree, batch and admissibility
+rules, oracle/treecode.py) to FP32 accuracy, and the direct operator to within the treecode's
+approximation error; theta -> 0 must reduce it to the direct sum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import treecode as tc
+from paper_1301_5914_gb300 import hobi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    # level 4, radius 10: 2562 targets (11 batches, the last one ragged), 20480 nodes
+    V, F, N = synth.icosphere(4, 10.0)
+    Q = synth.ball_charges(10, 8.0, 2)
+    orc = oracle.Problem(V, F, N, Q, 1.0, 80.0, 0.1257)
+    u_sol = orc.gmres(1e-8)[0]
+    return V, F, N, Q, orc, u_sol
+
+
+@pytest.mark.parametrize("degree,theta", [(4, 0.8), (6, 0.7)])
+def test_fast_matvec_matches_oracle_treecode(sphere, degree, theta):
+    V, F, N, Q, orc, u_sol = sphere
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", fast_degree=degree, fast_theta=theta)
+    st = {}
+    tc.treecode_far(orc, u_sol, degree, theta, stats=st)
+    info = s.fast_info()
+    assert info["batches"] == st["batches"] == 11
+    assert info["approx_pairs"] > 0
+    # the same interaction lists, up to nodes within rounding of a split plane
+    assert abs(info["direct_pairs"] - st["direct_pairs"]) <= 0.01 * st["direct_pairs"]
+    assert abs(info["approx_pairs"] - st["approx_pairs"]) <= 0.01 * st["approx_pairs"]
+    for u in (u_sol, np.random.default_rng(3).normal(size=2 * s.nv)):
+        ref = tc.treecode_matvec(orc, u, degree, theta)
+        got = s.matvec(u)
+        assert _rel(got, ref) <= 1e-5
+        # and the direct operator, within the approximation error (measured ~1e-6 here)
+        assert _rel(got, orc.matvec(u)) <= 3e-5
+
+
+def test_fast_small_theta_is_the_direct_sum(sphere):
+    V, F, N, Q, orc, u_sol = sphere
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", fast_degree=4, fast_theta=1e-3)
+    d = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32")
+    info = s.fast_info()
+    assert info["approx_pairs"] == 0 and info["direct_pairs"] == s.nv * s.n_nodes
+    u = np.random.default_rng(4).normal(size=2 * s.nv)
+    assert _rel(s.matvec(u), d.matvec(u)) <= 1e-6
+
+
+def test_fast_solve_energy_and_graphs(sphere):
+    V, F, N, Q, orc, u_sol = sphere
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", fast_degree=6, fast_theta=0.7)
+    g = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", fast_degree=6, fast_theta=0.7,
+                    use_graph=False)
+    phi, dphi, info = s.solve(1e-6)
+    phi2, dphi2, info2 = g.solve(1e-6)
+    assert info["converged"] and info["iterations"] == info2["iterations"]
+    assert np.array_equal(phi, phi2) and np.array_equal(dphi, dphi2)   # graph replay = direct launches
+    assert _rel(np.concatenate([phi, dphi]), u_sol) <= 1e-4
+    E = s.energy()
+    e_ref = orc.energy(u_sol)
+    assert abs(E - e_ref) <= 1e-5 * abs(e_ref)
+    # FP64 switches back to the direct FP64 far field
+    s.set_precision("fp64")
+    u = np.random.default_rng(5).normal(size=2 * s.nv)
+    ref = orc.matvec(u)
+    assert np.max(np.abs(s.matvec(u) - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_fast_larger_sphere_sampled_rows():
+    """Level 6 (the bench sizes: 40,962 targets x 327,680 nodes): sampled rows of the fast FP32
+    operator against the oracle's direct rows."""
+    V, F, N = synth.icosphere(6, 10.0)
+    Q = synth.ball_charges(10, 8.0, 2)
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", fast_degree=5, fast_theta=0.7)
+    info = s.fast_info()
+    assert info["direct_pairs"] + info["approx_pairs"] < 0.2 * s.nv * s.n_nodes
+    orc = oracle.Problem(V, F, N, Q, 1.0, 80.0, 0.1257)
+    phi, dphi, it = s.solve(1e-6)
+    assert it["converged"]
+    u = np.concatenate([phi, dphi])
+    rows = np.sort(np.random.default_rng(6).choice(s.nv, size=24, replace=False))
+    r1, r2 = orc.matvec_rows(u, rows)
+    Au = s.matvec(u)
+    assert np.max(np.abs(Au[rows] - r1)) <= 1e-4 * np.max(np.abs(r1))
+    assert np.max(np.abs(Au[s.nv + rows] - r2)) <= 1e-4 * np.max(np.abs(r2))
+
+
+def test_fast_option_errors(sphere):
+    V, F, N, Q, orc, u_sol = sphere
+    for kw in ({"fast_degree": 1}, {"fast_degree": 11}, {"fast_degree": 4, "fast_theta": 0.0},
+               {"fast_degree": 4, "fast_theta": 1.5}, {"fast_degree": 4, "scheme": "lobi"}):
+        with pytest.raises(hobi.HobiError):
+            hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", **kw)
