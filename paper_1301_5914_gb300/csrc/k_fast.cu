@@ -275,9 +275,11 @@ __global__ void k_fast_targets(int nv, const int* __restrict__ tmap, const float
 
 constexpr int kUpThreads = 128;
 constexpr int kMaxN1 = kFastMaxDegree + 1;
-constexpr int kUpPer = (kMaxN1 * kMaxN1 * kMaxN1 + kUpThreads - 1) / kUpThreads;
 
 // Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n1) of a proxy cluster.
+// Thread t owns proxies t + q kUpThreads, q < SLOTS = ceil((n+1)^3 / kUpThreads) (the slots past
+// the last proxy compute a duplicate and are not written).
+template <int SLOTS>
 __global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __restrict__ items,
                                                             const float* __restrict__ axes,
                                                             const float* __restrict__ half,
@@ -289,12 +291,12 @@ __global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __
   const float* ax = axes + (size_t)it.pc * 3 * n1;
   const float* hf = half + (size_t)it.pc * 3;
   const int n3 = n1 * n1 * n1;
-  float4 acc[kUpPer];
-  int pi[kUpPer], pj[kUpPer], pk[kUpPer];
+  float4 acc[SLOTS];
+  int pi[SLOTS], pj[SLOTS], pk[SLOTS];
 #pragma unroll
-  for (int q = 0; q < kUpPer; ++q) {
+  for (int q = 0; q < SLOTS; ++q) {
     acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int p = threadIdx.x + q * kUpThreads;
+    const int p = min(threadIdx.x + q * kUpThreads, n3 - 1);
     pi[q] = p / (n1 * n1);
     pj[q] = (p / n1) % n1;
     pk[q] = p % n1;
@@ -308,29 +310,24 @@ __global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __
       lagrange_row(-A.z, ax + n1, hf[1], n1, sL[1][threadIdx.x]);
       lagrange_row(-B.x, ax + 2 * n1, hf[2], n1, sL[2][threadIdx.x]);
       sq[threadIdx.x] = make_float4(B.z, C.x, C.z, D.x);  // sigma/eps, m
-    } else {
-      for (int k = 0; k < n1; ++k) sL[0][threadIdx.x][k] = sL[1][threadIdx.x][k] = sL[2][threadIdx.x][k] = 0.f;
-      sq[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     const int cnt = min(kUpThreads, it.n1 - c0);
     for (int t = 0; t < cnt; ++t) {
       const float4 q4 = sq[t];
 #pragma unroll
-      for (int q = 0; q < kUpPer; ++q) {
-        if (threadIdx.x + q * kUpThreads < n3) {
-          const float w = sL[0][t][pi[q]] * sL[1][t][pj[q]] * sL[2][t][pk[q]];
-          acc[q].x = fmaf(w, q4.x, acc[q].x);
-          acc[q].y = fmaf(w, q4.y, acc[q].y);
-          acc[q].z = fmaf(w, q4.z, acc[q].z);
-          acc[q].w = fmaf(w, q4.w, acc[q].w);
-        }
+      for (int q = 0; q < SLOTS; ++q) {
+        const float w = sL[0][t][pi[q]] * sL[1][t][pj[q]] * sL[2][t][pk[q]];
+        acc[q].x = fmaf(w, q4.x, acc[q].x);
+        acc[q].y = fmaf(w, q4.y, acc[q].y);
+        acc[q].z = fmaf(w, q4.z, acc[q].z);
+        acc[q].w = fmaf(w, q4.w, acc[q].w);
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < kUpPer; ++q) {
+  for (int q = 0; q < SLOTS; ++q) {
     const int p = threadIdx.x + q * kUpThreads;
     if (p < n3) partial[(size_t)blockIdx.x * n3 + p] = acc[q];
   }
@@ -406,7 +403,29 @@ cudaError_t launch_fast_upward(int nup, const FastUpItem* items, const float* ax
                                float4* srcf, int degree, float4* partial, int npc, const int2* pc_items,
                                const int* pc_off, double eps, cudaStream_t s) {
   const int n1 = degree + 1;
-  if (nup > 0) k_fast_upward<<<nup, kUpThreads, 0, s>>>(items, axes, half, srcf, n1, partial);
+  const int slots = (n1 * n1 * n1 + kUpThreads - 1) / kUpThreads;
+  if (nup > 0) {
+    switch (slots) {
+#define HOBI_UPWARD_CASE(S) \
+  case S:                   \
+    k_fast_upward<S><<<nup, kUpThreads, 0, s>>>(items, axes, half, srcf, n1, partial); \
+    break;
+      HOBI_UPWARD_CASE(1)
+      HOBI_UPWARD_CASE(2)
+      HOBI_UPWARD_CASE(3)
+      HOBI_UPWARD_CASE(4)
+      HOBI_UPWARD_CASE(5)
+      HOBI_UPWARD_CASE(6)
+      HOBI_UPWARD_CASE(7)
+      HOBI_UPWARD_CASE(8)
+      HOBI_UPWARD_CASE(9)
+      HOBI_UPWARD_CASE(10)
+      HOBI_UPWARD_CASE(11)
+#undef HOBI_UPWARD_CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
   const int64_t n = (int64_t)npc * n1 * n1 * n1;
   if (n > 0)
     k_fast_finish<<<nblk(n, 256), 256, 0, s>>>(npc, pc_items, pc_off, axes, partial, n1, (float)(1.0 - eps), srcf);
