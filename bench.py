@@ -253,6 +253,38 @@ def run_reference(args):
     return 0
 
 
+def fast_summation(hobi, arrays, e1, e2, ka, tol, stream, degree, theta):
+    """Treecode far field (degree, theta) against the direct FP32 far field on the same problem."""
+    import numpy as np
+    import torch
+
+    out = {"degree": degree, "theta": theta}
+    u = torch.as_tensor(np.random.default_rng(0).normal(size=2 * arrays[0].shape[0]), device=arrays[0].device)
+    res = {}
+    for name, kw in (("direct", {}), ("fast", {"fast_degree": degree, "fast_theta": theta})):
+        s = hobi.Solver(*arrays, e1, e2, ka, precision="fp32", stream=stream, **kw)
+        s.profile_enable(True)
+        for _ in range(3):
+            s.matvec(u)
+        s.profile_read()
+        for _ in range(10):
+            Au = s.matvec(u)
+        p = s.profile_read()
+        phi, dphi, info = s.solve(tol, 400)
+        res[name] = dict(ms=p["farfield_ms"] / p["launches"], Au=Au, phi=torch.cat([phi, dphi]), E=s.energy(),
+                         solve_ms=info["solve_ms"], it=info["iterations"], fi=s.fast_info(), nv=s.nv, nn=s.n_nodes)
+        s.close()
+    d, f = res["direct"], res["fast"]
+    rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    out.update(farfield_ms_direct=d["ms"], farfield_ms_fast=f["ms"], farfield_speedup=d["ms"] / f["ms"],
+               pairs_fraction=(f["fi"]["direct_pairs"] + f["fi"]["approx_pairs"]) / (d["nv"] * d["nn"]),
+               batches=f["fi"]["batches"], proxy_clusters=f["fi"]["proxy_clusters"],
+               solve_ms_direct=d["solve_ms"], solve_ms_fast=f["solve_ms"], iterations_direct=d["it"],
+               iterations_fast=f["it"], matvec_rel_l2_vs_direct=rel(f["Au"], d["Au"]),
+               u_rel_l2_vs_direct=rel(f["phi"], d["phi"]), E_rel_vs_direct=abs(f["E"] - d["E"]) / abs(d["E"]))
+    return out
+
+
 def run_ours(args):
     cfg, mols = make_workload(args.workload)  # before any CUDA call (the c4 generator uses a spawn pool)
     import numpy as np
@@ -387,6 +419,11 @@ def run_ours(args):
                         acc["E_rel_fp64_vs_kirkwood"] = abs(E64 - e_ex) / abs(e_ex)
                     except ImportError:
                         pass
+        # fast summation (treecode, beyond the paper) on the same inputs, outside the timed region:
+        # far-field time per matvec and solve time against the direct FP32 path, and its deviation
+        fast = None
+        if not batched and not args.no_fast:
+            fast = fast_summation(hobi, (Vd, Fd, Nd, Qd), e1, e2, ka, tol, stream, args.fast_degree, args.fast_theta)
         # end to end through the public API with host buffers, copies inside the timed region
         e2e_t, e2e_pairs = [], []
         for k in range(args.steps):
@@ -418,7 +455,7 @@ def run_ours(args):
                            pairs_per_step=pairs_per_step, gmres_iterations=iters[-1],
                            E_sol=(E.tolist() if batched else E)),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "gmres": gm, "accuracy": acc,
+            "gmres": gm, "accuracy": acc, "fast_summation": fast,
         }
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -436,6 +473,9 @@ def main(argv=None):
     ap.add_argument("--workload", choices=["c2l6", "c3", "c5", "c4"], default="c2l6")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain GMRES comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fast", action="store_true", help="skip the fast-summation (treecode) comparison")
+    ap.add_argument("--fast-degree", type=int, default=5)
+    ap.add_argument("--fast-theta", type=float, default=0.7)
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--ref-rows", type=int, default=1024)
     args = ap.parse_args(argv)

@@ -32,9 +32,9 @@ rules of this implementation:
   a Chebyshev point takes the Kronecker value). The approximated interaction is the pair
   formula above with the proxies as sources.
 
-Parity unpinned as an approximation of the paper (the paper has no fast summation); pinned to
-the direct sum (theta = 0 gives it exactly, the error falls with the degree) and to polynomial
-reproduction of the interpolation, in the tests.
+The paper prints no fast summation to compare with. The tests pin this module to the direct sum
+(a tiny theta gives it to rounding, the error falls with the degree) and to polynomial
+reproduction and partition of unity of the interpolation.
 """
 from __future__ import annotations
 

@@ -222,7 +222,7 @@ constexpr int kBatchFF32TilesPerTask = kTilesPerTask * kTile / kBatchFF32Tile;
 constexpr int kFastLeaf = 256;      // source-tree leaf size (nodes)
 constexpr int kFastBatch = 256;     // targets per batch = per evaluation block
 constexpr int kFastThreads = 32;    // evaluation block: one warp, 8 targets per thread
-constexpr int kFastSeg = 64;        // source entries per segment (one shared-memory stage)
+constexpr int kFastSeg = 128;       // source entries per segment (one shared-memory stage)
 constexpr int kFastUpSpan = 2048;   // nodes per upward work item
 constexpr int kFastMaxDegree = 10;
 struct FastTask {                   // one evaluation task: segments [s0, s1) of a batch
