@@ -63,6 +63,10 @@ MOLECULE = {"eps1": 2.0, "eps2": 80.0, "kappa": 0.1257, "gmres_tol": 1e-6,
 # 1 for P - 1, 4 for row 1, 3 for S, 2 for the 1/r^3 factors, 6 for the vector accumulation)
 OPS_PER_PAIR = 30
 MUFU_PER_PAIR = 2  # rsqrt.approx + ex2.approx
+# XU (MUFU) issue rate per SM per clock, from the far-field capture's counters: 0.217 XU warp
+# instructions per cycle per SM were 22.5 % of sm__inst_executed_pipe_xu's peak, i.e. about one
+# warp instruction (32 lanes) per cycle per SM.
+MUFU_LANES_PER_SM = 32
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "farfield32_c2_ico6_traffic.txt")
 FARFIELD_SRC = [os.path.join(ROOT, "paper_1301_5914_gb300", "csrc", f) for f in ("k_farfield.cu", "ff_body.cuh")]
 
@@ -206,8 +210,9 @@ def _traffic_per_launch():
     return None
 
 
-def cpu_oracle_sample(V, F, N, Q, rows: int, params=None, seed: int = 0):
-    """Time the FP64 oracle's matvec on `rows` sampled rows of the workload (bounded CPU work)."""
+def cpu_oracle_sample(V, F, N, Q, rows: int, params=None, seed: int = 0, threads: int = 0):
+    """Time the FP64 oracle's matvec on `rows` sampled rows of the workload (bounded CPU work),
+    on all host cores or on `threads` threads."""
     import numpy as np
 
     import oracle
@@ -218,11 +223,19 @@ def cpu_oracle_sample(V, F, N, Q, rows: int, params=None, seed: int = 0):
     u = rng.normal(size=2 * prob.nv)
     rows = min(rows, prob.nv)
     sel = np.sort(rng.choice(prob.nv, size=rows, replace=False))
-    t0 = time.perf_counter()
-    prob.matvec_rows(u, sel)
-    dt = time.perf_counter() - t0
+    all_threads = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
+    try:
+        used = oracle.num_threads()
+        t0 = time.perf_counter()
+        prob.matvec_rows(u, sel)
+        dt = time.perf_counter() - t0
+    finally:
+        if threads:
+            oracle.set_num_threads(all_threads)
     pairs = rows * 4.0 * prob.nf
-    return pairs / dt, dt, pairs, oracle.num_threads()
+    return pairs / dt, dt, pairs, used
 
 
 def run_reference(args):
@@ -387,7 +400,7 @@ def run_ours(args):
             "pairs_per_s": pairs_per_launch / avg_launch_s,
             "avg_launch_ms": avg_launch_s * 1e3,
             "frac_at_median_clock": achieved / (sms * 128 * fobs * 1e6 / 1e9),
-            "mufu_frac": pairs_per_launch * MUFU_PER_PAIR / avg_launch_s / (sms * 16 * fmax * 1e6),
+            "mufu_frac": pairs_per_launch * MUFU_PER_PAIR / avg_launch_s / (sms * MUFU_LANES_PER_SM * fmax * 1e6),
             "farfield_share_of_step": ff_ms / total_ms,
         }
         # FP64 plain path on the same inputs (outside the timed region): GMRES time to 1e-6
@@ -443,9 +456,14 @@ def run_ours(args):
             big = max(range(len(mols)), key=lambda i: mols[i][1].shape[0])
             V, F, N, Q = mols[big]
             val, dt, pairs, cores = cpu_oracle_sample(V, F, N, Q, args.cpu_rows, cfg)
+            val1, dt1, pairs1, _ = cpu_oracle_sample(V, F, N, Q, max(8, args.cpu_rows // 16), cfg, seed=1, threads=1)
             cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"{min(args.cpu_rows, V.shape[0])} of {V.shape[0]} matvec rows x {4 * F.shape[0]} "
-                             f"nodes ({pairs:.3g} pairs, {dt:.1f} s)" + (f", molecule {big}" if batched else "")}
+                             f"nodes ({pairs:.3g} pairs, {dt:.1f} s)" + (f", molecule {big}" if batched else ""),
+                   "value_1_thread": val1,
+                   "sample_1_thread": f"{max(8, args.cpu_rows // 16)} rows ({pairs1:.3g} pairs, {dt1:.1f} s)",
+                   # the oracle's time for the whole timed step at its measured rate (pairs / rate)
+                   "step_s_extrapolated": pairs_per_step / val}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

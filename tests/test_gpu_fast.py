@@ -111,3 +111,14 @@ def test_fast_option_errors(sphere):
                {"fast_degree": 4, "fast_theta": 1.5}, {"fast_degree": 4, "scheme": "lobi"}):
         with pytest.raises(hobi.HobiError):
             hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", **kw)
+
+
+def test_fast_unscaled_mode_kappa_zero():
+    """kappa = 0 runs the unscaled-coordinate variant of the evaluation kernel."""
+    V, F, N = synth.icosphere(4, 10.0)
+    Q = synth.ball_charges(10, 8.0, 2)
+    orc = oracle.Problem(V, F, N, Q, 1.0, 80.0, 0.0)
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.0, precision="fp32", fast_degree=5, fast_theta=0.7)
+    assert s.fast_info()["approx_pairs"] > 0
+    u = np.random.default_rng(7).normal(size=2 * s.nv)
+    assert _rel(s.matvec(u), tc.treecode_matvec(orc, u, 5, 0.7)) <= 1e-5
