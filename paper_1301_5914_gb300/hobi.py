@@ -138,7 +138,9 @@ class Solver:
 
     V [n_v,3], F [n_f,3] int32, N [n_v,3], charges [n_c,4]: all numpy arrays
     (host mode) or all CUDA torch tensors (device mode). scheme "hobi" (the paper's method) or
-    "lobi" (its low-order comparison scheme: unknowns at the n_f face centroids).
+    "lobi" (its low-order comparison scheme: unknowns at the n_f face centroids). fast_degree > 0
+    replaces the FP32 far field by a treecode of that interpolation degree with admissibility
+    parameter fast_theta (hobi_options.fast_degree / fast_theta).
     """
 
     def __init__(self, V, F, N, charges, eps1: float, eps2: float, kappa: float, precision: str = "fp32",

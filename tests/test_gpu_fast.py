@@ -122,3 +122,29 @@ def test_fast_unscaled_mode_kappa_zero():
     assert s.fast_info()["approx_pairs"] > 0
     u = np.random.default_rng(7).normal(size=2 * s.nv)
     assert _rel(s.matvec(u), tc.treecode_matvec(orc, u, 5, 0.7)) <= 1e-5
+
+
+def test_fast_tiny_mesh_is_direct():
+    """42 vertices, 320 nodes: one batch, no admissible cluster; the treecode is the direct sum."""
+    V, F, N = synth.icosphere(1, 1.0)
+    Q = synth.ball_charges(3, 0.6, 5)
+    s = hobi.Solver(V, F, N, Q, 2.0, 80.0, 1.0, precision="fp32", fast_degree=4)
+    d = hobi.Solver(V, F, N, Q, 2.0, 80.0, 1.0, precision="fp32")
+    info = s.fast_info()
+    assert info["batches"] == 1 and info["approx_pairs"] == 0
+    u = np.random.default_rng(8).normal(size=2 * s.nv)
+    assert _rel(s.matvec(u), d.matvec(u)) <= 1e-6
+
+
+def test_fast_molecular_surface_matches_oracle_treecode():
+    """A synthetic molecular surface (irregular mesh, eps1 = 2) against the oracle treecode."""
+    V, F, N, Q = synth.synthetic_molecule(200, 11)
+    orc = oracle.Problem(V, F, N, Q, 2.0, 80.0, 0.1257)
+    s = hobi.Solver(V, F, N, Q, 2.0, 80.0, 0.1257, precision="fp32", fast_degree=5, fast_theta=0.8)
+    st = {}
+    u = np.random.default_rng(9).normal(size=2 * s.nv)
+    tc.treecode_far(orc, u, 5, 0.8, stats=st)
+    info = s.fast_info()
+    assert info["batches"] == st["batches"] and info["approx_pairs"] > 0
+    assert abs(info["approx_pairs"] - st["approx_pairs"]) <= 0.01 * st["approx_pairs"]
+    assert _rel(s.matvec(u), tc.treecode_matvec(orc, u, 5, 0.8)) <= 1e-5
