@@ -92,8 +92,10 @@ typedef struct {
   int32_t fast_degree; /* 0 (default): the FP32 far field is summed directly over every node, as in
                           the paper. 2..10: fast summation by a barycentric Lagrange treecode of
                           this interpolation degree (beyond the paper, which names fast summation
-                          as future work; see hobi_fast_info). FP32_BULK precision, HOBI scheme,
-                          single-molecule handles only; the FP64 path stays direct. */
+                          as future work; see hobi_fast_info). FP32_BULK precision, HOBI scheme;
+                          the FP64 path stays direct. In a batch, a molecule uses it when it has
+                          at least 4096 collocation points and its plan needs at most 0.6 of the
+                          direct pair evaluations; the others stay direct. */
   double fast_theta;   /* treecode admissibility parameter in (0, 1] (default 0.7): a source
                           cluster C of more than (n+1)^3 nodes acts on a target batch B through its
                           (n+1)^3 Chebyshev proxy points when r_B + r_C < theta |c_B - c_C| */

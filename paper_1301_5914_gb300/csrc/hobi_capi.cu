@@ -79,6 +79,9 @@ struct hobi_ctx {
   FastUpItem* fast_up = nullptr;
   float *fast_axes = nullptr, *fast_half = nullptr;
   float4 *fast_src = nullptr, *fast_tgt = nullptr, *fast_partial = nullptr;
+  std::vector<FastTask> fast_tasks_h;  // host copies, for a batch that merges this molecule's plan
+  std::vector<FastUpItem> fast_up_h;
+  std::vector<int64_t> fast_task_cost_h;  // source entries of each task
   std::vector<void*> allocs;
   // inputs and geometry
   double *V = nullptr, *Nin = nullptr, *Nv = nullptr, *Q = nullptr;
@@ -256,7 +259,8 @@ struct hobi_ctx {
     return HOBI_OK;
   }
   // Treecode plan (host) from the FP64 node and vertex coordinates, uploaded with its buffers.
-  int setup_fast() {
+  // piece_sources > 0: evaluation pieces of about that many source entries (batch use).
+  int setup_fast(int piece_sources = 0) {
     std::vector<double> hy(3 * (size_t)n_nodes), hx(3 * (size_t)nv), hc(3);
     HOBI_CK(cudaMemcpyAsync(hy.data(), ny, sizeof(double) * hy.size(), cudaMemcpyDeviceToHost, stream));
     HOBI_CK(cudaMemcpyAsync(hx.data(), V, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost, stream));
@@ -265,7 +269,7 @@ struct hobi_ctx {
     fast_grid = num_sms * fast_eval_blocks_per_sm(kappa);
     FastPlanHost P;
     build_fast_plan(hy.data(), (int)n_nodes, hx.data(), (int)nv, hc.data(), xs, fast_degree, fast_theta, fast_grid,
-                    &P);
+                    piece_sources, &P);
     const int n3 = (fast_degree + 1) * (fast_degree + 1) * (fast_degree + 1);
     fast_chunks = P.chunks;
     fast_ntasks = (int)P.tasks.size();
@@ -275,6 +279,14 @@ struct hobi_ctx {
     fast_nseg = (int)P.seg.size();
     fast_direct_pairs = P.direct_pairs;
     fast_approx_pairs = P.approx_pairs;
+    fast_tasks_h = P.tasks;
+    fast_up_h = P.up;
+    fast_task_cost_h.clear();
+    for (const FastTask& t : P.tasks) {
+      int64_t c = 0;
+      for (int q = t.s0; q < t.s1; ++q) c += P.seg[q].y;
+      fast_task_cost_h.push_back(c);
+    }
     HOBI_TRY(upload(&fast_pos, P.node_pos));
     HOBI_TRY(upload(&fast_tmap, P.tmap));
     HOBI_TRY(upload(&fast_batch, P.batch));
@@ -1226,6 +1238,12 @@ struct hobi_batch_ctx {
   bool capturing = false, have_solution = false;
   int64_t launches = 0;
   int ff_grid[2] = {1, 1};
+  // fast summation of the FP32 far field for the molecules big enough to gain from it
+  int fast_degree = 0, nfup = 0, nfpcs = 0;
+  double fast_theta = 0.7;
+  FastUpItemB* fup = nullptr;
+  FastPCB* fpcs = nullptr;
+  std::vector<double> pairs32;  // FP32 pair evaluations per molecule and far-field launch
   // far-field timing (events around each launch; external event nodes inside captured graphs)
   bool prof = false, prof_pending = false;
   cudaEvent_t pev[2] = {nullptr, nullptr};
@@ -1235,8 +1253,11 @@ struct hobi_batch_ctx {
   double active_pairs() const {
     double p = 0.0;
     for (int i = 0; i < nmol; ++i)
-      if (!ms_host || (!ms_host[i].converged && !ms_host[i].breakdown)) p += (double)mols_h[i].nv * mols_h[i].n_nodes;
+      if (!ms_host || (!ms_host[i].converged && !ms_host[i].breakdown)) p += mol_pairs(i);
     return p;
+  }
+  double mol_pairs(int i) const {
+    return precision == HOBI_FP32_BULK ? pairs32[i] : (double)mols_h[i].nv * mols_h[i].n_nodes;
   }
   int prof_collect() {
     if (!prof_pending) return HOBI_OK;
@@ -1284,6 +1305,10 @@ struct hobi_batch_ctx {
         if (!e) HOBI_CK(cudaEventCreate(&e));
       HOBI_CK(cudaEventRecordWithFlags(pev[0], stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     }
+    if (fp32 && nfup > 0) {  // proxy densities of the molecules that use fast summation
+      HOBI_CK(launch_fast_upward_batch(nfup, fup, nfpcs, fpcs, mols, mask, fast_degree, eps, stream));
+      if (!capturing) launches += 2;
+    }
     HOBI_CK(launch_farfield_batch(fp32, mols, tasks[fp32], ntasks[fp32], counter, mask, eps, kappa, ff_grid[fp32],
                                   ff_err, stream));
     if (prof) {
@@ -1294,14 +1319,14 @@ struct hobi_batch_ctx {
         prof_pending = true;
       }
     }
-    HOBI_CK(launch_combine_batch(mols, nmol, vert_off, total_verts, u, kptr, ld, Au, mask, stream));
+    HOBI_CK(launch_combine_batch(mols, nmol, vert_off, total_verts, u, kptr, ld, Au, mask, fp32, stream));
     if (!capturing) launches += 3;
     return HOBI_OK;
   }
 
   double active_pairs_all() const {
     double p = 0.0;
-    for (int i = 0; i < nmol; ++i) p += (double)mols_h[i].nv * mols_h[i].n_nodes;
+    for (int i = 0; i < nmol; ++i) p += mol_pairs(i);
     return p;
   }
 
@@ -1350,7 +1375,7 @@ struct hobi_batch_ctx {
       prof_pending = true;
     }
     HOBI_CK(cudaGraphLaunch(gx, stream));
-    launches += kIterationKernels;
+    launches += kIterationKernels + (pi && nfup > 0 ? 2 : 0);
     return HOBI_OK;
   }
   int read_state() {
@@ -1413,6 +1438,7 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   hobi_options so = o;
   so.restart = 1;      // the batch owns the Krylov workspace
   so.use_graph = 0;
+  so.fast_degree = 0;  // the batch decides per molecule and builds the plans below
   for (int m = 0; m < nmol; ++m) {
     const int64_t nv = v_off[m + 1] - v_off[m], nf = f_off[m + 1] - f_off[m], nc = c_off[m + 1] - c_off[m];
     hobi_t h = nullptr;
@@ -1425,6 +1451,9 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   B->vert_off_h.assign(nmol + 1, 0);
   B->node_off_h.assign(nmol + 1, 0);
   std::vector<FFTask> tl[2];
+  std::vector<int64_t> cost[2];  // source entries per task (all tasks have the same target count)
+  std::vector<FastUpItemB> fup_h;
+  std::vector<FastPCB> fpcs_h;
   for (int m = 0; m < nmol; ++m) {
     hobi_ctx* h = B->subs[m];
     MolDesc d;
@@ -1435,14 +1464,54 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
     d.u_off = B->N;
     const int n_tiles = (int)(h->n_pad / kTile);
     d.chunks = (n_tiles + kTilesPerTask - 1) / kTilesPerTask;
-    HOBI_TRY(B->alloc(&d.part, (size_t)d.chunks * 2 * h->nv));
+    d.fast = 0;
+    d.fchunks = 0;
+    d.fpos = nullptr; d.fsrc = nullptr; d.ftgt = nullptr; d.ftmap = nullptr; d.fseg = nullptr; d.fbatch = nullptr;
+    d.faxes = nullptr; d.fhalf = nullptr; d.fpartial = nullptr; d.fpcitems = nullptr; d.fpcoff = nullptr;
+    double pairs = (double)h->nv * h->n_nodes;
+    if (B->fast_degree > 0 && h->nv >= kFastMinTargets) {
+      h->fast_degree = B->fast_degree;
+      h->fast_theta = B->fast_theta;
+      HOBI_TRY(h->setup_fast(kFastPieceSources));
+      const double fp = (double)(h->fast_direct_pairs + h->fast_approx_pairs);
+      if (fp <= kFastMaxFraction * pairs) {  // worth it: use the treecode for this molecule
+        d.fast = 1;
+        d.fchunks = h->fast_chunks;
+        d.fpos = h->fast_pos; d.fsrc = h->fast_src; d.ftgt = h->fast_tgt; d.ftmap = h->fast_tmap;
+        d.fseg = h->fast_seg; d.fbatch = h->fast_batch; d.faxes = h->fast_axes; d.fhalf = h->fast_half;
+        d.fpartial = h->fast_partial; d.fpcitems = h->fast_pcitems; d.fpcoff = h->fast_pcoff;
+        pairs = fp;
+        for (size_t i = 0; i < h->fast_up_h.size(); ++i) {
+          const FastUpItem& it = h->fast_up_h[i];
+          fup_h.push_back({m, it.pc, it.n0, it.n1, (int)i});
+        }
+        for (int pc = 0; pc < h->fast_npc; ++pc) fpcs_h.push_back({m, pc});
+      } else {
+        h->fast_degree = 0;
+      }
+    }
+    B->pairs32.push_back(pairs);
+    HOBI_TRY(B->alloc(&d.part, (size_t)std::max(d.chunks, d.fchunks) * 2 * h->nv));
     for (int fp32 = 0; fp32 < 2; ++fp32) {
+      if (fp32 && d.fast) {
+        for (size_t q = 0; q < h->fast_tasks_h.size(); ++q) {
+          const FastTask& t = h->fast_tasks_h[q];
+          tl[fp32].push_back({m, t.batch, t.s0, t.s1, t.chunk, 1});
+          cost[fp32].push_back(h->fast_task_cost_h[q]);
+        }
+        continue;
+      }
       const int per_block = fp32 ? kBatchFF32Threads * kFF32Targets : kFF64Threads * kFF64Targets;
       const int tiles = fp32 ? (int)(h->n_pad / kBatchFF32Tile) : n_tiles;
       const int tpt = fp32 ? kBatchFF32TilesPerTask : kTilesPerTask;
+      const int tile_nodes = fp32 ? kBatchFF32Tile : kTile;
       const int tt = (int)((h->nv + per_block - 1) / per_block);
       for (int bx = 0; bx < tt; ++bx)
-        for (int c = 0; c < d.chunks; ++c) tl[fp32].push_back({m, bx, c * tpt, std::min(tiles, (c + 1) * tpt), c});
+        for (int c = 0; c < d.chunks; ++c) {
+          const int t0 = c * tpt, t1 = std::min(tiles, (c + 1) * tpt);
+          tl[fp32].push_back({m, bx, t0, t1, c, 0});
+          cost[fp32].push_back((int64_t)(t1 - t0) * tile_nodes);
+        }
     }
     B->mols_h.push_back(d);
     B->N += 2 * h->nv;
@@ -1451,10 +1520,24 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   }
   B->total_verts = B->vert_off_h[nmol];
   B->total_nodes = B->node_off_h[nmol];
+  B->nfup = (int)fup_h.size();
+  B->nfpcs = (int)fpcs_h.size();
+  if (B->nfup > 0) {
+    HOBI_TRY(B->alloc(&B->fup, fup_h.size()));
+    HOBI_TRY(B->alloc(&B->fpcs, fpcs_h.size()));
+    HOBI_CK(cudaMemcpyAsync(B->fup, fup_h.data(), sizeof(FastUpItemB) * fup_h.size(), cudaMemcpyHostToDevice,
+                            B->stream));
+    HOBI_CK(cudaMemcpyAsync(B->fpcs, fpcs_h.data(), sizeof(FastPCB) * fpcs_h.size(), cudaMemcpyHostToDevice,
+                            B->stream));
+  }
   for (int fp32 = 0; fp32 < 2; ++fp32) {
     // longest tasks first, so the tail of the dynamic schedule is made of short ones
-    std::stable_sort(tl[fp32].begin(), tl[fp32].end(),
-                     [](const FFTask& a, const FFTask& b) { return (a.t1 - a.t0) > (b.t1 - b.t0); });
+    std::vector<int> ord(tl[fp32].size());
+    for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[fp32][a] > cost[fp32][b]; });
+    std::vector<FFTask> sorted;
+    for (int q : ord) sorted.push_back(tl[fp32][q]);
+    tl[fp32].swap(sorted);
     B->ntasks[fp32] = (int)tl[fp32].size();
     HOBI_TRY(B->alloc(&B->tasks[fp32], tl[fp32].size()));
     HOBI_CK(cudaMemcpyAsync(B->tasks[fp32], tl[fp32].data(), sizeof(FFTask) * tl[fp32].size(), cudaMemcpyHostToDevice,
@@ -1543,7 +1626,10 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
   if (opt) o = *opt;
   if (o.precision != HOBI_FP64 && o.precision != HOBI_FP32_BULK) return fail(HOBI_ERR_ARG, "unknown precision");
   if (o.scheme != HOBI_SCHEME_HOBI) return fail(HOBI_ERR_ARG, "the batch API supports the HOBI scheme only");
-  if (o.fast_degree != 0) return fail(HOBI_ERR_ARG, "the batch API evaluates the far field directly (fast_degree 0)");
+  if (o.fast_degree != 0 && (o.fast_degree < 2 || o.fast_degree > kFastMaxDegree))
+    return fail(HOBI_ERR_ARG, "fast_degree must be 0 (direct far field) or 2..10");
+  if (o.fast_degree != 0 && !(o.fast_theta > 0.0 && o.fast_theta <= 1.0))
+    return fail(HOBI_ERR_ARG, "fast_theta must be in (0, 1]");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
   int dev = o.device;
@@ -1563,6 +1649,8 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
   B->nmol = n_mol;
   B->eps = eps2 / eps1;
   B->kappa = kappa;
+  B->fast_degree = o.fast_degree;
+  B->fast_theta = o.fast_theta;
   int r = HOBI_OK;
   do {
     cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);

@@ -192,9 +192,24 @@ struct MolDesc {          // one molecule's device tables (owned by its single-m
   double eps;
   double xs;              // FP32 coordinate scale (ff32_coord_scale)
   int64_t u_off;          // offset of the molecule's 2 nv block in the concatenated vectors
+  // fast summation of the FP32 far field (fast = 1): tree-ordered node and proxy entries,
+  // batch-ordered targets, segments, and the upward tables; fchunks partial rows
+  int fast, fchunks;
+  const int* fpos;
+  float4* fsrc;
+  const float4* ftgt;
+  const int* ftmap;
+  const int2* fseg;
+  const int2* fbatch;
+  const float* faxes;
+  const float* fhalf;
+  float4* fpartial;
+  const int2* fpcitems;
+  const int* fpcoff;
 };
 struct FFTask {           // one persistent far-field work item: targets of block bx, tiles [t0, t1)
   int mol, bx, t0, t1, chunk;
+  int fast;               // 1: treecode task, bx = batch, [t0, t1) = segments of the molecule's list
 };
 struct Segment {          // piece of the concatenated vector inside one molecule
   int64_t start;
@@ -225,6 +240,11 @@ constexpr int kFastThreads = 32;    // evaluation block: one warp, 8 targets per
 constexpr int kFastSeg = 128;       // source entries per segment (one shared-memory stage)
 constexpr int kFastUpSpan = 2048;   // nodes per upward work item
 constexpr int kFastMaxDegree = 10;
+// batches: a molecule uses the treecode when it has at least kFastMinTargets targets and its plan
+// needs at most kFastMaxFraction of the direct pair evaluations; pieces of ~kFastPieceSources
+constexpr int kFastMinTargets = 4096;
+constexpr double kFastMaxFraction = 0.6;
+constexpr int kFastPieceSources = 4096;
 struct FastTask {                   // one evaluation task: segments [s0, s1) of a batch
   int batch, s0, s1, chunk;
 };
@@ -247,9 +267,10 @@ struct FastPlanHost {
   std::vector<float> half;          // per proxy cluster: 3 scaled half-extents
 };
 // y: nodes (n_nodes x 3), x: targets (nv x 3), FP64 absolute coordinates; center and xs as for
-// the FP32 tables. resident_blocks sizes the task split.
-int build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const double* center, double xs,
-                    int degree, double theta, int resident_blocks, FastPlanHost* out);
+// the FP32 tables. Each batch's segment list is cut into `chunks` pieces: enough for about 8
+// tasks per resident block (piece_sources = 0), or pieces of about piece_sources source entries.
+void build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const double* center, double xs,
+                     int degree, double theta, int resident_blocks, int piece_sources, FastPlanHost* out);
 cudaError_t launch_fast_targets(int nv, const int* tmap, const float4* tgt32, float4* tgtf, cudaStream_t s);
 cudaError_t launch_fast_upward(int nup, const FastUpItem* items, const float* axes, const float* half,
                                float4* srcf, int degree, float4* partial, int npc, const int2* pc_items,
@@ -258,6 +279,16 @@ cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, int* counter, co
                              const float4* srcf, const float4* tgtf, const int* tmap, int nv, double eps,
                              double kappa, double* part, int grid, int* err, cudaStream_t s);
 int fast_eval_blocks_per_sm(double kappa);
+// batched treecode upward pass: work items and proxy clusters of every fast molecule
+struct FastUpItemB {
+  int mol, pc, n0, n1, local;  // local: the item's index among its molecule's items
+};
+struct FastPCB {
+  int mol, pc;
+};
+cudaError_t launch_fast_upward_batch(int nitems, const FastUpItemB* items, int npcs, const FastPCB* pcs,
+                                     const MolDesc* mols, const MolState* ms, int degree, double eps,
+                                     cudaStream_t s);
 
 cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const int64_t* node_off, int64_t total_nodes,
                                 const double* u, const int* kptr, int64_t ld, const MolState* ms, cudaStream_t s);
@@ -266,7 +297,7 @@ cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* 
 int farfield_batch_blocks_per_sm(bool fp32, double kappa);
 cudaError_t launch_combine_batch(const MolDesc* mols, int nmol, const int64_t* vert_off, int64_t total_verts,
                                  const double* u, const int* kptr, int64_t ld, double* Au, const MolState* ms,
-                                 cudaStream_t s);
+                                 bool fp32, cudaStream_t s);
 cudaError_t launch_bdots(const double* Vb, int64_t ld, const double* w, const Segment* seg, int nseg,
                          const BatchState* gs, const MolState* ms, int self, double* part, cudaStream_t s);
 cudaError_t launch_breduce(const double* part, int nseg, const int* mol_seg, int nmol, int m, const BatchState* gs,

@@ -59,7 +59,8 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
   const double* um = u + (kptr ? (int64_t)(*kptr) * ld : 0) + d.u_off;
   int node = (int)(g - node_off[m]);
   if (fp32)
-    ff::gather32_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.xs, d.src32, node);
+    ff::gather32_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.xs, d.fast ? d.fsrc : d.src32,
+                      d.fast ? d.fpos[node] : node);
   else
     ff::gather64_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, d.src64);
 }
@@ -72,7 +73,8 @@ template <bool KS>
 __global__ void __launch_bounds__(kBatchFF32Threads, 8)
     k_farfield_batch32(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, int ntasks, int* counter,
                        const MolState* ms, FF32Consts cs, int* err) {
-  __shared__ __align__(128) float4 sh[2 * 4 * kBatchFF32Tile];
+  constexpr int kStage = kFastSeg > kBatchFF32Tile ? kFastSeg : kBatchFF32Tile;  // entries per stage
+  __shared__ __align__(128) float4 sh[2 * 4 * kStage];
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_task;
   if (threadIdx.x == 0) ff::tile_barriers_init(bars);
@@ -87,8 +89,17 @@ __global__ void __launch_bounds__(kBatchFF32Threads, 8)
     const FFTask tk = tasks[t];
     if (mol_done(ms, tk.mol)) continue;
     const MolDesc& d = mols[tk.mol];
-    const bool ok = ff::ff32_block<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kBatchFF32Tile>(
-        d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs, d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh, bars, phases, err);
+    double* out = d.part + (size_t)tk.chunk * 2 * d.nv;
+    bool ok;
+    if (tk.fast) {  // treecode task: a piece of a batch's segment list (direct leaves and proxies)
+      const int2 b = d.fbatch[tk.bx];
+      const ff::SegmentTiles tiles{d.fsrc, d.fseg + tk.t0};
+      ok = ff::ff32_core<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kFastSeg>(
+          d.ftgt, b.x, b.x + b.y, d.ftmap, d.nv, tiles, tk.t1 - tk.t0, cs, out, sh, bars, phases, err);
+    } else {
+      ok = ff::ff32_block<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kBatchFF32Tile>(
+          d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs, out, tk.bx, sh, bars, phases, err);
+    }
     if (!ok) return;  // the tile pipeline timed out (reported through err)
   }
 }
@@ -114,15 +125,15 @@ __global__ void __launch_bounds__(kFF64Threads)
 
 __global__ void k_combine_batch(const MolDesc* __restrict__ mols, int nmol, const int64_t* vert_off,
                                 int64_t total_verts, const double* __restrict__ u, const int* kptr, int64_t ld,
-                                double* __restrict__ Au, const MolState* ms) {
+                                double* __restrict__ Au, const MolState* ms, bool fp32) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= total_verts) return;
   int m = find_segment(vert_off, nmol, g);
   if (mol_done(ms, m)) return;
   const MolDesc& d = mols[m];
   const double* um = u + (kptr ? (int64_t)(*kptr) * ld : 0) + d.u_off;
-  ff::combine_vertex((int)(g - vert_off[m]), d.nv, d.chunks, d.part, d.F, d.inc_ptr, d.inc_face, d.corr, d.eps, um,
-                     Au + d.u_off);
+  ff::combine_vertex((int)(g - vert_off[m]), d.nv, fp32 && d.fast ? d.fchunks : d.chunks, d.part, d.F, d.inc_ptr,
+                     d.inc_face, d.corr, d.eps, um, Au + d.u_off);
 }
 
 // ---------------------------------------------------------------- GMRES on the concatenation
@@ -343,8 +354,9 @@ int farfield_batch_blocks_per_sm(bool fp32, double kappa) {
 
 cudaError_t launch_combine_batch(const MolDesc* mols, int nmol, const int64_t* vert_off, int64_t total_verts,
                                  const double* u, const int* kptr, int64_t ld, double* Au, const MolState* ms,
-                                 cudaStream_t s) {
-  k_combine_batch<<<nblk(total_verts, 256), 256, 0, s>>>(mols, nmol, vert_off, total_verts, u, kptr, ld, Au, ms);
+                                 bool fp32, cudaStream_t s) {
+  k_combine_batch<<<nblk(total_verts, 256), 256, 0, s>>>(mols, nmol, vert_off, total_verts, u, kptr, ld, Au, ms,
+                                                         fp32);
   return cudaGetLastError();
 }
 

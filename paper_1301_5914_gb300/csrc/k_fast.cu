@@ -141,8 +141,8 @@ void traverse(const std::vector<Cluster>& cl, int ci, const double* cb, double r
 
 }  // namespace
 
-int build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const double* center, double xs,
-                    int degree, double theta, int resident_blocks, FastPlanHost* out) {
+void build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const double* center, double xs,
+                     int degree, double theta, int resident_blocks, int piece_sources, FastPlanHost* out) {
   FastPlanHost& F = *out;
   F = FastPlanHost();
   const int n1 = degree + 1, n3 = n1 * n1 * n1;
@@ -211,7 +211,15 @@ int build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const
   }
   // batches and tasks: every batch's segment list cut into `chunks` pieces of equal work
   const int nb = (int)bt.size();
-  int chunks = (8 * resident_blocks + nb - 1) / nb;
+  int chunks;
+  if (piece_sources > 0) {
+    int64_t total = 0;
+    for (const auto& sg : segs)
+      for (const int2& e : sg) total += e.y;
+    chunks = (int)((total / std::max(nb, 1) + piece_sources - 1) / piece_sources);
+  } else {
+    chunks = (8 * resident_blocks + nb - 1) / nb;
+  }
   chunks = std::max(1, std::min(chunks, 256));
   F.chunks = chunks;
   std::vector<std::pair<int64_t, FastTask>> tl;
@@ -236,7 +244,6 @@ int build_fast_plan(const double* y, int n_nodes, const double* x, int nv, const
   std::stable_sort(tl.begin(), tl.end(), [](const std::pair<int64_t, FastTask>& a,
                                              const std::pair<int64_t, FastTask>& b2) { return a.first > b2.first; });
   for (auto& t : tl) F.tasks.push_back(t.second);
-  return 0;
 }
 
 // ------------------------------------------------------------------ device
@@ -276,20 +283,16 @@ __global__ void k_fast_targets(int nv, const int* __restrict__ tmap, const float
 constexpr int kUpThreads = 128;
 constexpr int kMaxN1 = kFastMaxDegree + 1;
 
-// Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n1) of a proxy cluster.
-// Thread t owns proxies t + q kUpThreads, q < SLOTS = ceil((n+1)^3 / kUpThreads) (the slots past
-// the last proxy compute a duplicate and are not written).
+// Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n1) (tree order) of a proxy
+// cluster with Chebyshev axes ax and half-extents hf, to out[p], p < (n+1)^3. Thread t owns
+// proxies t + q kUpThreads, q < SLOTS = ceil((n+1)^3 / kUpThreads) (the slots past the last
+// proxy compute a duplicate and are not written).
 template <int SLOTS>
-__global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __restrict__ items,
-                                                            const float* __restrict__ axes,
-                                                            const float* __restrict__ half,
-                                                            const float4* __restrict__ srcf, int n1,
-                                                            float4* __restrict__ partial) {
+__device__ __forceinline__ void upward_block(int n0, int n1_end, const float* __restrict__ ax,
+                                             const float* __restrict__ hf, const float4* __restrict__ srcf, int n1,
+                                             float4* __restrict__ out) {
   __shared__ float sL[3][kUpThreads][kMaxN1];
   __shared__ float4 sq[kUpThreads];
-  const FastUpItem it = items[blockIdx.x];
-  const float* ax = axes + (size_t)it.pc * 3 * n1;
-  const float* hf = half + (size_t)it.pc * 3;
   const int n3 = n1 * n1 * n1;
   float4 acc[SLOTS];
   int pi[SLOTS], pj[SLOTS], pk[SLOTS];
@@ -301,9 +304,9 @@ __global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __
     pj[q] = (p / n1) % n1;
     pk[q] = p % n1;
   }
-  for (int c0 = it.n0; c0 < it.n1; c0 += kUpThreads) {
+  for (int c0 = n0; c0 < n1_end; c0 += kUpThreads) {
     const int node = c0 + threadIdx.x;
-    if (node < it.n1) {
+    if (node < n1_end) {
       const float4 A = srcf[4 * (size_t)node], B = srcf[4 * (size_t)node + 1];
       const float4 C = srcf[4 * (size_t)node + 2], D = srcf[4 * (size_t)node + 3];
       lagrange_row(-A.x, ax, hf[0], n1, sL[0][threadIdx.x]);
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __
       sq[threadIdx.x] = make_float4(B.z, C.x, C.z, D.x);  // sigma/eps, m
     }
     __syncthreads();
-    const int cnt = min(kUpThreads, it.n1 - c0);
+    const int cnt = min(kUpThreads, n1_end - c0);
     for (int t = 0; t < cnt; ++t) {
       const float4 q4 = sq[t];
 #pragma unroll
@@ -329,19 +332,40 @@ __global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __
 #pragma unroll
   for (int q = 0; q < SLOTS; ++q) {
     const int p = threadIdx.x + q * kUpThreads;
-    if (p < n3) partial[(size_t)blockIdx.x * n3 + p] = acc[q];
+    if (p < n3) out[p] = acc[q];
   }
+}
+
+template <int SLOTS>
+__global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __restrict__ items,
+                                                            const float* __restrict__ axes,
+                                                            const float* __restrict__ half,
+                                                            const float4* __restrict__ srcf, int n1,
+                                                            float4* __restrict__ partial) {
+  const FastUpItem it = items[blockIdx.x];
+  upward_block<SLOTS>(it.n0, it.n1, axes + (size_t)it.pc * 3 * n1, half + (size_t)it.pc * 3, srcf, n1,
+                      partial + (size_t)blockIdx.x * n1 * n1 * n1);
+}
+
+// The same over the work items of every molecule of a batch that uses fast summation.
+template <int SLOTS>
+__global__ void __launch_bounds__(kUpThreads) k_fast_upward_batch(const FastUpItemB* __restrict__ items,
+                                                                  const MolDesc* __restrict__ mols,
+                                                                  const MolState* ms, int n1) {
+  const FastUpItemB it = items[blockIdx.x];
+  if (ms && (ms[it.mol].converged || ms[it.mol].breakdown)) return;
+  const MolDesc& d = mols[it.mol];
+  upward_block<SLOTS>(it.n0, it.n1, d.faxes + (size_t)it.pc * 3 * n1, d.fhalf + (size_t)it.pc * 3, d.fsrc, n1,
+                      d.fpartial + (size_t)it.local * n1 * n1 * n1);
 }
 
 // Proxy source entries: partial densities of each cluster's items added in order, written in
 // the FP32 source layout {-s, sigma/eps, m, sigma/eps - sigma} after the tree-ordered nodes.
-__global__ void k_fast_finish(int npc, const int2* __restrict__ pc_items, const int* __restrict__ pc_off,
-                              const float* __restrict__ axes, const float4* __restrict__ partial, int n1,
-                              float one_minus_eps, float4* __restrict__ srcf) {
+__device__ __forceinline__ void finish_entry(int pc, int p, const int2* __restrict__ pc_items,
+                                             const int* __restrict__ pc_off, const float* __restrict__ axes,
+                                             const float4* __restrict__ partial, int n1, float one_minus_eps,
+                                             float4* __restrict__ srcf) {
   const int n3 = n1 * n1 * n1;
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= (int64_t)npc * n3) return;
-  const int pc = (int)(g / n3), p = (int)(g % n3);
   const int2 r = pc_items[pc];
   float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int q = 0; q < r.y; ++q) {
@@ -359,6 +383,26 @@ __global__ void k_fast_finish(int npc, const int2* __restrict__ pc_items, const 
   o[1] = make_float4(-z, -z, s.x, s.x);
   o[2] = make_float4(s.y, s.y, s.z, s.z);
   o[3] = make_float4(s.w, s.w, sd, sd);
+}
+
+__global__ void k_fast_finish(int npc, const int2* __restrict__ pc_items, const int* __restrict__ pc_off,
+                              const float* __restrict__ axes, const float4* __restrict__ partial, int n1,
+                              float one_minus_eps, float4* __restrict__ srcf) {
+  const int n3 = n1 * n1 * n1;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)npc * n3) return;
+  finish_entry((int)(g / n3), (int)(g % n3), pc_items, pc_off, axes, partial, n1, one_minus_eps, srcf);
+}
+
+__global__ void k_fast_finish_batch(int npcs, const FastPCB* __restrict__ pcs, const MolDesc* __restrict__ mols,
+                                    const MolState* ms, int n1, float one_minus_eps) {
+  const int n3 = n1 * n1 * n1;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)npcs * n3) return;
+  const FastPCB e = pcs[g / n3];
+  if (ms && (ms[e.mol].converged || ms[e.mol].breakdown)) return;
+  const MolDesc& d = mols[e.mol];
+  finish_entry(e.pc, (int)(g % n3), d.fpcitems, d.fpcoff, d.faxes, d.fpartial, n1, one_minus_eps, d.fsrc);
 }
 
 // Persistent evaluation: one-warp blocks pull (batch, piece) tasks from an atomic counter and
@@ -444,6 +488,38 @@ cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, int* counter, co
   else
     k_fast_eval<false><<<grid, kFastThreads, 0, s>>>(tasks, ntasks, counter, batch, seg, srcf, tgtf, tmap, nv, cs,
                                                       part, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fast_upward_batch(int nitems, const FastUpItemB* items, int npcs, const FastPCB* pcs,
+                                     const MolDesc* mols, const MolState* ms, int degree, double eps,
+                                     cudaStream_t s) {
+  const int n1 = degree + 1;
+  const int slots = (n1 * n1 * n1 + kUpThreads - 1) / kUpThreads;
+  if (nitems > 0) {
+    switch (slots) {
+#define HOBI_UPWARD_CASE(S) \
+  case S:                   \
+    k_fast_upward_batch<S><<<nitems, kUpThreads, 0, s>>>(items, mols, ms, n1); \
+    break;
+      HOBI_UPWARD_CASE(1)
+      HOBI_UPWARD_CASE(2)
+      HOBI_UPWARD_CASE(3)
+      HOBI_UPWARD_CASE(4)
+      HOBI_UPWARD_CASE(5)
+      HOBI_UPWARD_CASE(6)
+      HOBI_UPWARD_CASE(7)
+      HOBI_UPWARD_CASE(8)
+      HOBI_UPWARD_CASE(9)
+      HOBI_UPWARD_CASE(10)
+      HOBI_UPWARD_CASE(11)
+#undef HOBI_UPWARD_CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
+  const int64_t n = (int64_t)npcs * n1 * n1 * n1;
+  if (n > 0) k_fast_finish_batch<<<nblk(n, 256), 256, 0, s>>>(npcs, pcs, mols, ms, n1, (float)(1.0 - eps));
   return cudaGetLastError();
 }
 

@@ -354,11 +354,13 @@ class BatchSolver:
 
     molecules: list of (V, F, N, charges) numpy arrays (host mode). With device=True the
     concatenated inputs are first placed in CUDA torch tensors (device-pointer mode).
+    fast_degree > 0: molecules with at least 4096 collocation points whose treecode plan pays off
+    use fast summation for the FP32 far field (hobi_options.fast_degree / fast_theta).
     """
 
     def __init__(self, molecules, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
                  restart: int = 50, use_graph: bool = True, device_mode: bool = False, stream=None,
-                 device_arrays=None):
+                 device_arrays=None, fast_degree: int = 0, fast_theta: float = 0.7):
         lib = load_library()
         self._lib = lib
         V = np.ascontiguousarray(np.concatenate([m[0] for m in molecules]), dtype=np.float64)
@@ -378,6 +380,8 @@ class BatchSolver:
         opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
         opt.restart = int(restart)
         opt.use_graph = 1 if use_graph else 0
+        opt.fast_degree = int(fast_degree)
+        opt.fast_theta = float(fast_theta)
         if self.device_mode:
             import torch
 
