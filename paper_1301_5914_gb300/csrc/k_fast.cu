@@ -294,11 +294,11 @@ __device__ __forceinline__ void upward_block(int n0, int n1_end, const float* __
   __shared__ float sL[3][kUpThreads][kMaxN1];
   __shared__ float4 sq[kUpThreads];
   const int n3 = n1 * n1 * n1;
-  float4 acc[SLOTS];
+  float2 acc01[SLOTS], acc23[SLOTS];  // (sigma/eps, m_x), (m_y, m_z) as packed pairs
   int pi[SLOTS], pj[SLOTS], pk[SLOTS];
 #pragma unroll
   for (int q = 0; q < SLOTS; ++q) {
-    acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc01[q] = acc23[q] = make_float2(0.f, 0.f);
     const int p = min(threadIdx.x + q * kUpThreads, n3 - 1);
     pi[q] = p / (n1 * n1);
     pj[q] = (p / n1) % n1;
@@ -318,13 +318,13 @@ __device__ __forceinline__ void upward_block(int n0, int n1_end, const float* __
     const int cnt = min(kUpThreads, n1_end - c0);
     for (int t = 0; t < cnt; ++t) {
       const float4 q4 = sq[t];
+      const float2 q01 = make_float2(q4.x, q4.y), q23 = make_float2(q4.z, q4.w);
 #pragma unroll
       for (int q = 0; q < SLOTS; ++q) {
         const float w = sL[0][t][pi[q]] * sL[1][t][pj[q]] * sL[2][t][pk[q]];
-        acc[q].x = fmaf(w, q4.x, acc[q].x);
-        acc[q].y = fmaf(w, q4.y, acc[q].y);
-        acc[q].z = fmaf(w, q4.z, acc[q].z);
-        acc[q].w = fmaf(w, q4.w, acc[q].w);
+        const float2 ww = make_float2(w, w);
+        acc01[q] = __ffma2_rn(ww, q01, acc01[q]);
+        acc23[q] = __ffma2_rn(ww, q23, acc23[q]);
       }
     }
     __syncthreads();
@@ -332,7 +332,7 @@ __device__ __forceinline__ void upward_block(int n0, int n1_end, const float* __
 #pragma unroll
   for (int q = 0; q < SLOTS; ++q) {
     const int p = threadIdx.x + q * kUpThreads;
-    if (p < n3) out[p] = acc[q];
+    if (p < n3) out[p] = make_float4(acc01[q].x, acc01[q].y, acc23[q].x, acc23[q].y);
   }
 }
 
