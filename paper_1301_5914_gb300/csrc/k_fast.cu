@@ -281,6 +281,7 @@ __global__ void k_fast_targets(int nv, const int* __restrict__ tmap, const float
 }
 
 constexpr int kUpThreads = 128;
+constexpr int kUpNodes = 64;  // nodes whose basis values are staged per pass
 constexpr int kMaxN1 = kFastMaxDegree + 1;
 
 // Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n1) (tree order) of a proxy
@@ -291,37 +292,41 @@ template <int SLOTS>
 __device__ __forceinline__ void upward_block(int n0, int n1_end, const float* __restrict__ ax,
                                              const float* __restrict__ hf, const float4* __restrict__ srcf, int n1,
                                              float4* __restrict__ out) {
-  __shared__ float sL[3][kUpThreads][kMaxN1];
-  __shared__ float4 sq[kUpThreads];
+  // per node of the current pass: L_i(x) L_j(y) at i n1 + j, L_k(z), and the densities
+  __shared__ float sLxy[kUpNodes][kMaxN1 * kMaxN1];
+  __shared__ float sLz[kUpNodes][kMaxN1];
+  __shared__ float4 sq[kUpNodes];
   const int n3 = n1 * n1 * n1;
   float2 acc01[SLOTS], acc23[SLOTS];  // (sigma/eps, m_x), (m_y, m_z) as packed pairs
-  int pi[SLOTS], pj[SLOTS], pk[SLOTS];
+  int pij[SLOTS], pk[SLOTS];
 #pragma unroll
   for (int q = 0; q < SLOTS; ++q) {
     acc01[q] = acc23[q] = make_float2(0.f, 0.f);
     const int p = min(threadIdx.x + q * kUpThreads, n3 - 1);
-    pi[q] = p / (n1 * n1);
-    pj[q] = (p / n1) % n1;
+    pij[q] = p / n1;
     pk[q] = p % n1;
   }
-  for (int c0 = n0; c0 < n1_end; c0 += kUpThreads) {
+  for (int c0 = n0; c0 < n1_end; c0 += kUpNodes) {
     const int node = c0 + threadIdx.x;
-    if (node < n1_end) {
+    if (threadIdx.x < kUpNodes && node < n1_end) {
       const float4 A = srcf[4 * (size_t)node], B = srcf[4 * (size_t)node + 1];
       const float4 C = srcf[4 * (size_t)node + 2], D = srcf[4 * (size_t)node + 3];
-      lagrange_row(-A.x, ax, hf[0], n1, sL[0][threadIdx.x]);
-      lagrange_row(-A.z, ax + n1, hf[1], n1, sL[1][threadIdx.x]);
-      lagrange_row(-B.x, ax + 2 * n1, hf[2], n1, sL[2][threadIdx.x]);
+      float Lx[kMaxN1], Ly[kMaxN1];
+      lagrange_row(-A.x, ax, hf[0], n1, Lx);
+      lagrange_row(-A.z, ax + n1, hf[1], n1, Ly);
+      lagrange_row(-B.x, ax + 2 * n1, hf[2], n1, sLz[threadIdx.x]);
+      for (int a = 0; a < n1; ++a)
+        for (int b = 0; b < n1; ++b) sLxy[threadIdx.x][a * n1 + b] = Lx[a] * Ly[b];
       sq[threadIdx.x] = make_float4(B.z, C.x, C.z, D.x);  // sigma/eps, m
     }
     __syncthreads();
-    const int cnt = min(kUpThreads, n1_end - c0);
+    const int cnt = min(kUpNodes, n1_end - c0);
     for (int t = 0; t < cnt; ++t) {
       const float4 q4 = sq[t];
       const float2 q01 = make_float2(q4.x, q4.y), q23 = make_float2(q4.z, q4.w);
 #pragma unroll
       for (int q = 0; q < SLOTS; ++q) {
-        const float w = sL[0][t][pi[q]] * sL[1][t][pj[q]] * sL[2][t][pk[q]];
+        const float w = sLxy[t][pij[q]] * sLz[t][pk[q]];
         const float2 ww = make_float2(w, w);
         acc01[q] = __ffma2_rn(ww, q01, acc01[q]);
         acc23[q] = __ffma2_rn(ww, q23, acc23[q]);
