@@ -171,7 +171,17 @@ void build_fast_plan(const double* y, int n_nodes, const double* x, int nv, cons
     traverse(cl, 0, cb, rb, theta, n3, direct, approx);
     const int64_t nb = bt[b].end - bt[b].begin;
     for (int ci : direct) {
-      for (int s = cl[ci].begin; s < cl[ci].end; s += kFastSeg) segs[b].push_back({s, std::min(kFastSeg, cl[ci].end - s)});
+      // leaves adjacent in tree order are adjacent in memory: fill the previous segment first
+      int s = cl[ci].begin;
+      if (!segs[b].empty()) {
+        int2& last = segs[b].back();
+        if (last.x + last.y == s && last.y < kFastSeg) {
+          const int add = std::min(kFastSeg - last.y, cl[ci].end - s);
+          last.y += add;
+          s += add;
+        }
+      }
+      for (; s < cl[ci].end; s += kFastSeg) segs[b].push_back({s, std::min(kFastSeg, cl[ci].end - s)});
       F.direct_pairs += nb * (cl[ci].end - cl[ci].begin);
     }
     for (int ci : approx) {
