@@ -228,10 +228,10 @@ struct MolState {
 constexpr int kSegLen = 4096;
 constexpr int kTilesPerTask = 16;  // kTile-node tiles per task (FP64), i.e. 4096 source nodes
 // Batched FP32 far field: one-warp persistent blocks with 8 targets per thread (256 targets per
-// task, so a molecule wastes at most 255 target slots) and 64-node tiles, 64 of them per task
+// task, so a molecule wastes at most 255 target slots) and 128-node tiles, 32 of them per task
 // (the same 4096 source nodes per chunk as the FP64 tasks).
 constexpr int kBatchFF32Threads = 32;
-constexpr int kBatchFF32Tile = 64;
+constexpr int kBatchFF32Tile = 128;
 constexpr int kBatchFF32TilesPerTask = kTilesPerTask * kTile / kBatchFF32Tile;
 // ---- fast summation of the far field (k_fast.cu): barycentric Lagrange treecode ----
 constexpr int kFastLeaf = 256;      // source-tree leaf size (nodes)

@@ -175,6 +175,16 @@ def test_batch_fast_equals_single_molecule_fast():
         else:
             assert _rel(Au[off:off + n], ref_direct) <= 2e-5
         off += n
+    # FP64 keeps the direct far field for every molecule
+    b.set_precision("fp64")
+    A64 = b.matvec(u)
+    off = 0
+    for m in mols:
+        n = 2 * m[0].shape[0]
+        ref = hobi.Solver(*m, 1.0, 80.0, 0.1257, precision="fp64").matvec(u[off:off + n])
+        assert np.max(np.abs(A64[off:off + n] - ref)) <= 1e-12 * np.max(np.abs(ref))
+        off += n
+    b.set_precision("fp32")
     phis, dphis, info = b.solve(1e-6)
     assert info["converged"]
     E = b.energy()
