@@ -1,0 +1,93 @@
+"""Parity at the full sizes of the two largest workloads, in the launch configurations bench.py
+times: the C5 two-globule complex (59,888 vertices x 479,088 nodes) and the C4 batch of 64
+molecules, on sampled rows the oracle evaluates one by one; and the empty-charge edge case.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1301_5914_gb300 import hobi, synth
+
+pytestmark = pytest.mark.gpu
+
+KAPPA = 0.1257
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _rows(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False))
+
+
+def _check_rows(Au, orc, u, rows, tol):
+    r1, r2 = orc.matvec_rows(u, rows)
+    nv = orc.nv
+    assert np.max(np.abs(Au[rows] - r1)) <= tol * np.max(np.abs(r1))
+    assert np.max(np.abs(Au[nv + rows] - r2)) <= tol * np.max(np.abs(r2))
+
+
+def test_c5_complex_sampled_rows():
+    V, F, N, Q = synth.two_globule_complex(3000, 51, 52, n_faces=120000)
+    s = hobi.Solver(V, F, N, Q, 2.0, 80.0, KAPPA, precision="fp32")
+    assert s.nv > 55000 and s.n_nodes > 450000
+    phi, dphi, info = s.solve(1e-6, 400)
+    assert info["converged"]
+    u = np.concatenate([phi, dphi])
+    orc = oracle.Problem(V, F, N, Q, 2.0, 80.0, KAPPA)
+    rows = np.concatenate([_rows(s.nv, 16, 1), [0, s.nv - 1]])
+    # FP32 pair terms carry ~1e-7 relative error each; over 479,088 nodes the K3/K4 row cancels
+    # more than at smaller sizes (sum of |terms| / |sum| grows), so the bound is 5e-5 of max |row|
+    _check_rows(s.matvec(u), orc, u, rows, 5e-5)
+    s.set_precision("fp64")
+    _check_rows(s.matvec(u), orc, u, rows, 1e-10)
+    # the solved energy against the oracle's energy of the same surface potential
+    s.set_precision("fp32")
+    s.set_solution(u)
+    e_ref = orc.energy(u)
+    assert abs(s.energy() - e_ref) <= 1e-5 * abs(e_ref)
+
+
+def _c4_member(m):
+    n_atoms = int(round(np.exp(np.random.default_rng(1000 + m).uniform(np.log(50), np.log(2000)))))
+    return synth.synthetic_molecule(n_atoms, 1000 + m)
+
+
+def test_c4_batch_sampled_rows():
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        mols = pool.map(_c4_member, range(64))
+    b = hobi.BatchSolver(mols, 2.0, 80.0, KAPPA, precision="fp32")
+    phis, dphis, info = b.solve(1e-6, 400)
+    assert info["converged"]
+    E = b.energy()
+    sizes = [m[0].shape[0] for m in mols]
+    for k in (int(np.argmax(sizes)), int(np.argsort(sizes)[32]), int(np.argmin(sizes))):
+        V, F, N, Q = mols[k]
+        orc = oracle.Problem(V, F, N, Q, 2.0, 80.0, KAPPA)
+        u = np.concatenate([np.asarray(phis[k]), np.asarray(dphis[k])])
+        # the batch's operator on this molecule's block, sampled rows against the oracle
+        uc = np.zeros(2 * b.nv_total)
+        o = 2 * int(b.vert_off[k])
+        uc[o:o + u.size] = u
+        Au = b.matvec(uc)[o:o + u.size]
+        rows = np.concatenate([_rows(orc.nv, min(12, orc.nv), 2 + k), [0, orc.nv - 1]])
+        _check_rows(Au, orc, u, np.unique(rows), 5e-5)
+        e_ref = orc.energy(u)
+        assert abs(E[k] - e_ref) <= 1e-5 * abs(e_ref)
+
+
+def test_no_charges_gives_zero_solution_and_energy():
+    V, F, N = synth.icosphere(3, 5.0)
+    s = hobi.Solver(V, F, N, np.zeros((0, 4)), 1.0, 80.0, KAPPA, precision="fp32")
+    assert np.all(s.rhs() == 0.0)
+    phi, dphi, info = s.solve(1e-6, 50, raise_on_fail=False)
+    assert np.all(phi == 0.0) and np.all(dphi == 0.0)
+    assert s.energy() == 0.0
