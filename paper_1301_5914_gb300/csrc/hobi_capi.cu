@@ -11,8 +11,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hobi.h"
 #include "hobi_internal.cuh"
+
+namespace {
+// NVTX range around a public call (no-op unless a profiler is attached), so nsys / ncu timelines
+// show setup, matvec, solve and energy phases by name.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 using namespace hobi;
 
@@ -826,6 +837,7 @@ extern "C" {
 int hobi_setup(const double* vertices, int64_t n_v, const int32_t* faces, int64_t n_f, const double* vertex_normals,
                const double* charges, int64_t n_c, double eps1, double eps2, double kappa, const hobi_options* opt,
                hobi_t* out) {
+  NvtxRange nvtx_range("hobi_setup");
   return create_handle(vertices, n_v, faces, n_f, vertex_normals, charges, n_c, eps1, eps2, kappa, opt, false, out);
 }
 
@@ -847,6 +859,7 @@ int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_no
 }
 
 int hobi_matvec(hobi_t h, const double* u, double* Au) {
+  NvtxRange nvtx_range("hobi_matvec");
   if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
   if (!u || !Au) return fail(HOBI_ERR_ARG, "u and Au must be non-NULL");
   if (u == Au) return fail(HOBI_ERR_ARG, "Au must not alias u");
@@ -972,11 +985,13 @@ int solve_impl(hobi_t h, const double* u0, bool warm, double tol, int32_t max_it
 extern "C" {
 
 int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, hobi_solve_info* info) {
+  NvtxRange nvtx_range("hobi_solve");
   return solve_impl(h, nullptr, false, tol, max_it, phi, dphi, info);
 }
 
 int hobi_solve_from(hobi_t h, const double* u0, double tol, int32_t max_it, double* phi, double* dphi,
                     hobi_solve_info* info) {
+  NvtxRange nvtx_range("hobi_solve_from");
   return solve_impl(h, u0, true, tol, max_it, phi, dphi, info);
 }
 
@@ -1000,6 +1015,7 @@ int hobi_get_solution(hobi_t h, double* u) {
 }
 
 int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, double* phi) {
+  NvtxRange nvtx_range("hobi_reaction_potential");
   if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
   if (n_points < 0 || (n_points > 0 && (!points || !phi))) return fail(HOBI_ERR_ARG, "bad points/phi arguments");
   if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
@@ -1019,6 +1035,7 @@ int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, do
 }
 
 int hobi_energy(hobi_t h, double* e_sol) {
+  NvtxRange nvtx_range("hobi_energy");
   if (!h || !e_sol) return fail(HOBI_ERR_ARG, "NULL argument");
   if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
   DeviceGuard guard(h->device);
@@ -1606,6 +1623,7 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
                      const int64_t* face_offsets, const double* vertex_normals, const double* charges,
                      const int64_t* charge_offsets, double eps1, double eps2, double kappa, const hobi_options* opt,
                      hobi_batch_t* out) {
+  NvtxRange nvtx_range("hobi_setup_batch");
   g_err.clear();
   if (!out) return fail(HOBI_ERR_ARG, "out handle pointer is NULL");
   *out = nullptr;
@@ -1696,6 +1714,7 @@ int hobi_batch_set_precision(hobi_batch_t B, int32_t precision) {
 }
 
 int hobi_matvec_batch(hobi_batch_t B, const double* u, double* Au) {
+  NvtxRange nvtx_range("hobi_matvec_batch");
   if (!B || !u || !Au) return fail(HOBI_ERR_ARG, "NULL argument");
   if (u == Au) return fail(HOBI_ERR_ARG, "Au must not alias u");
   DeviceGuard guard(B->device);
@@ -1717,6 +1736,7 @@ int hobi_matvec_batch(hobi_batch_t B, const double* u, double* Au) {
 
 int hobi_solve_batch(hobi_batch_t B, double tol, int32_t max_it, double* phi, double* dphi, int32_t* iterations,
                      int32_t* status, hobi_solve_info* info) {
+  NvtxRange nvtx_range("hobi_solve_batch");
   if (!B) return fail(HOBI_ERR_ARG, "NULL handle");
   if (!(tol > 0.0) || max_it < 1) return fail(HOBI_ERR_ARG, "need tol > 0 and max_it >= 1");
   DeviceGuard guard(B->device);
@@ -1798,6 +1818,7 @@ int hobi_solve_batch(hobi_batch_t B, double tol, int32_t max_it, double* phi, do
 }
 
 int hobi_energy_batch(hobi_batch_t B, double* e_sol) {
+  NvtxRange nvtx_range("hobi_energy_batch");
   if (!B || !e_sol) return fail(HOBI_ERR_ARG, "NULL argument");
   if (!B->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve_batch first");
   DeviceGuard guard(B->device);
