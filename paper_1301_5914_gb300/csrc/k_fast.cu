@@ -294,84 +294,117 @@ constexpr int kUpThreads = 128;
 constexpr int kUpNodes = 64;  // nodes whose basis values are staged per pass
 constexpr int kMaxN1 = kFastMaxDegree + 1;
 
-// Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n1) (tree order) of a proxy
-// cluster with Chebyshev axes ax and half-extents hf, to out[p], p < (n+1)^3. Thread t owns
-// proxies t + q kUpThreads, q < SLOTS = ceil((n+1)^3 / kUpThreads) (the slots past the last
-// proxy compute a duplicate and are not written).
-template <int SLOTS>
-__device__ __forceinline__ void upward_block(int n0, int n1_end, const float* __restrict__ ax,
-                                             const float* __restrict__ hf, const float4* __restrict__ srcf, int n1,
-                                             float4* __restrict__ out) {
-  // per node of the current pass: L_i(x) L_j(y) at i n1 + j, L_k(z), and the densities
-  __shared__ float sLxy[kUpNodes][kMaxN1 * kMaxN1];
-  __shared__ float sLz[kUpNodes][kMaxN1];
-  __shared__ float4 sq[kUpNodes];
-  const int n3 = n1 * n1 * n1;
-  float2 acc01[SLOTS], acc23[SLOTS];  // (sigma/eps, m_x), (m_y, m_z) as packed pairs
-  int pij[SLOTS], pk[SLOTS];
+// Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n_end) (tree order) of a
+// proxy cluster with Chebyshev axes ax and half-extents hf, to out[p], p = (i N1 + j) N1 + k.
+// Nodes go in passes of kUpNodes: the first kUpNodes threads stage each node's L_i(x) L_j(y)
+// products, its L_k(z) row and its densities in shared memory. Thread t then owns the pair
+// ij = t mod N1^2 and the node group g = t / N1^2 (G groups): it accumulates the N1 proxies
+// (ij, k) over the nodes of its group, one shared load of L_i L_j per node and the L_k row
+// reused for all k; the groups are added in shared memory at the end.
+template <int N1>
+struct UpwardShape {
+  static constexpr int N2 = N1 * N1, N3 = N2 * N1;
+  static constexpr int G = kUpThreads / N2;  // node groups (N2 <= 121 < kUpThreads)
+  static constexpr size_t stage_bytes = sizeof(float4) * kUpNodes + sizeof(float) * kUpNodes * (N2 + N1);
+  static constexpr size_t bytes = stage_bytes + (G > 1 ? sizeof(float4) * G * N3 : 0);
+};
+
+template <int N1>
+__device__ __forceinline__ void upward_block(int n0, int n_end, const float* __restrict__ ax,
+                                             const float* __restrict__ hf, const float4* __restrict__ srcf,
+                                             float4* __restrict__ out, float* dyn) {
+  using S = UpwardShape<N1>;
+  constexpr int N2 = S::N2, N3 = S::N3, G = S::G;
+  float4* sq = reinterpret_cast<float4*>(dyn);
+  float* sLxy = dyn + 4 * kUpNodes;      // [kUpNodes][N2]
+  float* sLz = sLxy + kUpNodes * N2;     // [kUpNodes][N1]
+  const int ij = threadIdx.x % N2, g = threadIdx.x / N2;
+  const bool active = g < G;
+  float2 a01[N1], a23[N1];  // (sigma/eps, m_x), (m_y, m_z) of proxies (ij, k)
 #pragma unroll
-  for (int q = 0; q < SLOTS; ++q) {
-    acc01[q] = acc23[q] = make_float2(0.f, 0.f);
-    const int p = min(threadIdx.x + q * kUpThreads, n3 - 1);
-    pij[q] = p / n1;
-    pk[q] = p % n1;
-  }
-  for (int c0 = n0; c0 < n1_end; c0 += kUpNodes) {
+  for (int k = 0; k < N1; ++k) a01[k] = a23[k] = make_float2(0.f, 0.f);
+  for (int c0 = n0; c0 < n_end; c0 += kUpNodes) {
     const int node = c0 + threadIdx.x;
-    if (threadIdx.x < kUpNodes && node < n1_end) {
+    if (threadIdx.x < kUpNodes && node < n_end) {
       const float4 A = srcf[4 * (size_t)node], B = srcf[4 * (size_t)node + 1];
       const float4 C = srcf[4 * (size_t)node + 2], D = srcf[4 * (size_t)node + 3];
-      float Lx[kMaxN1], Ly[kMaxN1];
-      lagrange_row(-A.x, ax, hf[0], n1, Lx);
-      lagrange_row(-A.z, ax + n1, hf[1], n1, Ly);
-      lagrange_row(-B.x, ax + 2 * n1, hf[2], n1, sLz[threadIdx.x]);
-      for (int a = 0; a < n1; ++a)
-        for (int b = 0; b < n1; ++b) sLxy[threadIdx.x][a * n1 + b] = Lx[a] * Ly[b];
+      float Lx[N1], Ly[N1];
+      lagrange_row(-A.x, ax, hf[0], N1, Lx);
+      lagrange_row(-A.z, ax + N1, hf[1], N1, Ly);
+      lagrange_row(-B.x, ax + 2 * N1, hf[2], N1, sLz + threadIdx.x * N1);
+      float* row = sLxy + threadIdx.x * N2;
+#pragma unroll
+      for (int a = 0; a < N1; ++a)
+#pragma unroll
+        for (int b = 0; b < N1; ++b) row[a * N1 + b] = Lx[a] * Ly[b];
       sq[threadIdx.x] = make_float4(B.z, C.x, C.z, D.x);  // sigma/eps, m
     }
     __syncthreads();
-    const int cnt = min(kUpNodes, n1_end - c0);
-    for (int t = 0; t < cnt; ++t) {
-      const float4 q4 = sq[t];
-      const float2 q01 = make_float2(q4.x, q4.y), q23 = make_float2(q4.z, q4.w);
+    if (active) {
+      const int cnt = min(kUpNodes, n_end - c0);
+      for (int t = g; t < cnt; t += G) {
+        const float4 q4 = sq[t];
+        const float2 q01 = make_float2(q4.x, q4.y), q23 = make_float2(q4.z, q4.w);
+        const float wij = sLxy[t * N2 + ij];
+        const float* lz = sLz + t * N1;
 #pragma unroll
-      for (int q = 0; q < SLOTS; ++q) {
-        const float w = sLxy[t][pij[q]] * sLz[t][pk[q]];
-        const float2 ww = make_float2(w, w);
-        acc01[q] = __ffma2_rn(ww, q01, acc01[q]);
-        acc23[q] = __ffma2_rn(ww, q23, acc23[q]);
+        for (int k = 0; k < N1; ++k) {
+          const float w = wij * lz[k];
+          const float2 ww = make_float2(w, w);
+          a01[k] = __ffma2_rn(ww, q01, a01[k]);
+          a23[k] = __ffma2_rn(ww, q23, a23[k]);
+        }
       }
     }
     __syncthreads();
   }
+  if (G == 1) {
+    if (active)
 #pragma unroll
-  for (int q = 0; q < SLOTS; ++q) {
-    const int p = threadIdx.x + q * kUpThreads;
-    if (p < n3) out[p] = make_float4(acc01[q].x, acc01[q].y, acc23[q].x, acc23[q].y);
+      for (int k = 0; k < N1; ++k) out[ij * N1 + k] = make_float4(a01[k].x, a01[k].y, a23[k].x, a23[k].y);
+    return;
+  }
+  float4* red = reinterpret_cast<float4*>(reinterpret_cast<char*>(dyn) + S::stage_bytes);  // [G][N3]
+  if (active)
+#pragma unroll
+    for (int k = 0; k < N1; ++k) red[g * N3 + ij * N1 + k] = make_float4(a01[k].x, a01[k].y, a23[k].x, a23[k].y);
+  __syncthreads();
+  for (int p = threadIdx.x; p < N3; p += kUpThreads) {
+    float4 s = red[p];
+    for (int q = 1; q < G; ++q) {  // groups added in a fixed order
+      const float4 v = red[q * N3 + p];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    out[p] = s;
   }
 }
 
-template <int SLOTS>
+template <int N1>
 __global__ void __launch_bounds__(kUpThreads) k_fast_upward(const FastUpItem* __restrict__ items,
                                                             const float* __restrict__ axes,
                                                             const float* __restrict__ half,
-                                                            const float4* __restrict__ srcf, int n1,
+                                                            const float4* __restrict__ srcf,
                                                             float4* __restrict__ partial) {
+  extern __shared__ __align__(16) float dyn[];
   const FastUpItem it = items[blockIdx.x];
-  upward_block<SLOTS>(it.n0, it.n1, axes + (size_t)it.pc * 3 * n1, half + (size_t)it.pc * 3, srcf, n1,
-                      partial + (size_t)blockIdx.x * n1 * n1 * n1);
+  upward_block<N1>(it.n0, it.n1, axes + (size_t)it.pc * 3 * N1, half + (size_t)it.pc * 3, srcf,
+                   partial + (size_t)blockIdx.x * UpwardShape<N1>::N3, dyn);
 }
 
 // The same over the work items of every molecule of a batch that uses fast summation.
-template <int SLOTS>
+template <int N1>
 __global__ void __launch_bounds__(kUpThreads) k_fast_upward_batch(const FastUpItemB* __restrict__ items,
                                                                   const MolDesc* __restrict__ mols,
-                                                                  const MolState* ms, int n1) {
+                                                                  const MolState* ms) {
+  extern __shared__ __align__(16) float dyn[];
   const FastUpItemB it = items[blockIdx.x];
   if (ms && (ms[it.mol].converged || ms[it.mol].breakdown)) return;
   const MolDesc& d = mols[it.mol];
-  upward_block<SLOTS>(it.n0, it.n1, d.faxes + (size_t)it.pc * 3 * n1, d.fhalf + (size_t)it.pc * 3, d.fsrc, n1,
-                      d.fpartial + (size_t)it.local * n1 * n1 * n1);
+  upward_block<N1>(it.n0, it.n1, d.faxes + (size_t)it.pc * 3 * N1, d.fhalf + (size_t)it.pc * 3, d.fsrc,
+                   d.fpartial + (size_t)it.local * UpwardShape<N1>::N3, dyn);
 }
 
 // Proxy source entries: partial densities of each cluster's items added in order, written in
@@ -462,15 +495,12 @@ cudaError_t launch_fast_upward(int nup, const FastUpItem* items, const float* ax
                                float4* srcf, int degree, float4* partial, int npc, const int2* pc_items,
                                const int* pc_off, double eps, cudaStream_t s) {
   const int n1 = degree + 1;
-  const int slots = (n1 * n1 * n1 + kUpThreads - 1) / kUpThreads;
   if (nup > 0) {
-    switch (slots) {
-#define HOBI_UPWARD_CASE(S) \
-  case S:                   \
-    k_fast_upward<S><<<nup, kUpThreads, 0, s>>>(items, axes, half, srcf, n1, partial); \
+    switch (n1) {
+#define HOBI_UPWARD_CASE(N) \
+  case N:                   \
+    k_fast_upward<N><<<nup, kUpThreads, UpwardShape<N>::bytes, s>>>(items, axes, half, srcf, partial); \
     break;
-      HOBI_UPWARD_CASE(1)
-      HOBI_UPWARD_CASE(2)
       HOBI_UPWARD_CASE(3)
       HOBI_UPWARD_CASE(4)
       HOBI_UPWARD_CASE(5)
@@ -510,15 +540,12 @@ cudaError_t launch_fast_upward_batch(int nitems, const FastUpItemB* items, int n
                                      const MolDesc* mols, const MolState* ms, int degree, double eps,
                                      cudaStream_t s) {
   const int n1 = degree + 1;
-  const int slots = (n1 * n1 * n1 + kUpThreads - 1) / kUpThreads;
   if (nitems > 0) {
-    switch (slots) {
-#define HOBI_UPWARD_CASE(S) \
-  case S:                   \
-    k_fast_upward_batch<S><<<nitems, kUpThreads, 0, s>>>(items, mols, ms, n1); \
+    switch (n1) {
+#define HOBI_UPWARD_CASE(N) \
+  case N:                   \
+    k_fast_upward_batch<N><<<nitems, kUpThreads, UpwardShape<N>::bytes, s>>>(items, mols, ms); \
     break;
-      HOBI_UPWARD_CASE(1)
-      HOBI_UPWARD_CASE(2)
       HOBI_UPWARD_CASE(3)
       HOBI_UPWARD_CASE(4)
       HOBI_UPWARD_CASE(5)
