@@ -282,7 +282,9 @@ int hobi_solve_batch(hobi_batch_t b, double tol, int32_t max_it, double* phi, do
 int hobi_energy_batch(hobi_batch_t b, double* e_sol);
 
 /* Timing of the batched far-field launches, as hobi_profile_enable / hobi_profile_read
- * (pairs counts only the molecules still iterating at each launch). */
+ * (pairs counts only the molecules still iterating at each launch; for a molecule on fast
+ * summation, its node and proxy pair evaluations; the timed span includes the treecode's
+ * upward pass). */
 int hobi_batch_profile_enable(hobi_batch_t b, int32_t on);
 int hobi_batch_profile_read(hobi_batch_t b, double* farfield_ms, int64_t* launches, double* pairs);
 
