@@ -2,7 +2,8 @@
 one +1 e charge moved from the centre toward the surface, kappa = 1, eps = 80, HOBI-PB and
 LOBI-PB against the Kirkwood series, surface-potential error e_phi (Eq. eqerr1) per
 icosahedral level. The figure's data are not in the paper; the test checks the paper's
-observations that hold on uniform meshes and writes the table to gpurun_out/ when run there."""
+observations that hold on uniform meshes, and writes the table as JSON into the directory named
+by the environment variable HOBI_STUDY_OUT when it is set."""
 import json
 import os
 
@@ -45,10 +46,12 @@ def table():
             Q = synth.point_charge(x, 0.0, 0.0, 1.0)
             for scheme in ("hobi", "lobi"):
                 out[(scheme, L, x)] = _ephi(V, F, N, Q, scheme)
-    if os.path.isdir("gpurun_out"):
+    out_dir = os.environ.get("HOBI_STUDY_OUT")
+    if out_dir and os.path.isdir(out_dir):
         rows = [{"scheme": k[0], "level": k[1], "faces": 20 * 4 ** k[1], "x": k[2], "e_phi": v[0],
                  "iterations": v[1]} for k, v in sorted(out.items())]
-        json.dump(rows, open("gpurun_out/eccentric_sphere_study.json", "w"), indent=1)
+        with open(os.path.join(out_dir, "eccentric_sphere_study.json"), "w") as fh:
+            json.dump(rows, fh, indent=1)
     return out
 
 
