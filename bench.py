@@ -463,6 +463,14 @@ def run_ours(args):
             it64 = i64["iterations"].tolist() if batched else i64["iterations"]
             gm = {"fp32_bulk_s": i32["solve_ms"] / 1e3, "fp64_plain_s": i64["solve_ms"] / 1e3,
                   "iterations_fp32": it32, "iterations_fp64": it64, "speedup": i64["solve_ms"] / i32["solve_ms"]}
+            if not batched:  # mixed precision: FP32-bulk corrections, tolerance met on the FP64 operator
+                for rtol in (tol, 1e-10):
+                    sr = make("fp32")
+                    _, _, ir = sr.solve_refined(rtol, 8, 400)
+                    sr.close()
+                    gm[f"refined_to_{rtol:g}_s"] = ir["solve_ms"] / 1e3
+                    gm[f"refined_to_{rtol:g}_fp64_residual"] = ir["rel_residual"]
+                gm["refined_speedup_vs_fp64_plain"] = gm["fp64_plain_s"] / gm[f"refined_to_{tol:g}_s"]
             if batched:
                 p32, p64 = torch.cat(list(map(torch.as_tensor, p32))), torch.cat(list(map(torch.as_tensor, p64)))
                 d32, d64 = torch.cat(list(map(torch.as_tensor, d32))), torch.cat(list(map(torch.as_tensor, d64)))

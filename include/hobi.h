@@ -155,6 +155,18 @@ int hobi_rhs(hobi_t h, double* b);
 int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi,
                hobi_solve_info* info);
 
+/* Mixed-precision solve (iterative refinement; the paper has no counterpart, it works in FP64):
+ * starting from u = 0, each step forms the residual r = b - A u with the FP64 far field, stops when
+ * ||r|| / ||b|| <= tol, and otherwise solves A d = r with FP32-bulk GMRES to 1e-6 (at most max_it
+ * matvecs; fast summation when enabled) and sets u += d; at most max_refine corrections. The
+ * result meets tol on the FP64 operator, which plain FP32-bulk GMRES cannot below ~1e-6, at
+ * about one FP64 matvec per correction instead of one per Krylov iteration. The handle's
+ * precision is unchanged on return. info: iterations = FP32 Krylov iterations in total,
+ * rel_residual = the final FP64 residual, resid_history = the FP64 residual after each step
+ * (first entry 1). Returns HOBI_OK or HOBI_ERR_NOT_CONVERGED (u written either way). */
+int hobi_solve_refined(hobi_t h, double tol, int32_t max_refine, int32_t max_it, double* phi, double* dphi,
+                       hobi_solve_info* info);
+
 /* Warm start / resume: as hobi_solve, but GMRES starts from x0 = u0 (2 n_v doubles) or, when u0
  * is NULL, from the handle's current solution (a previous solve or hobi_set_solution; else
  * HOBI_ERR_STATE). The stopping test stays ||b - A u|| / ||b|| <= tol, so resuming a solve that

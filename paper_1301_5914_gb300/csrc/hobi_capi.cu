@@ -90,6 +90,9 @@ struct hobi_ctx {
   FastUpItem* fast_up = nullptr;
   float *fast_axes = nullptr, *fast_half = nullptr;
   float4 *fast_src = nullptr, *fast_tgt = nullptr, *fast_partial = nullptr;
+  // mixed-precision refinement (hobi_solve_refined): accumulated solution, residual, correction
+  double *ref_x = nullptr, *ref_r = nullptr, *ref_d = nullptr, *ref_scal = nullptr;
+  cudaEvent_t ref_t0 = nullptr, ref_t1 = nullptr;
   std::vector<FastTask> fast_tasks_h;  // host copies, for a batch that merges this molecule's plan
   std::vector<FastUpItem> fast_up_h;
   std::vector<int64_t> fast_task_cost_h;  // source entries of each task
@@ -969,7 +972,10 @@ int solve_impl(hobi_t h, const double* u0, bool warm, double tol, int32_t max_it
     info->converged = fs.converged;
     info->rel_residual = fs.rel;
     info->solve_ms = ms;
-    info->farfield_pairs = (double)(fs.it + 0) * (double)h->nv * (double)h->n_nodes;
+    const double per_matvec = h->fast_active(h->precision == HOBI_FP32_BULK)
+                                  ? (double)(h->fast_direct_pairs + h->fast_approx_pairs)
+                                  : (double)h->nv * (double)h->n_nodes;
+    info->farfield_pairs = (double)fs.it * per_matvec;
     if (info->resid_history && info->resid_capacity > 0) {
       int cnt = (int)hist.size() < info->resid_capacity ? (int)hist.size() : info->resid_capacity;
       for (int i = 0; i < cnt; ++i) info->resid_history[i] = hist[i];
@@ -980,6 +986,97 @@ int solve_impl(hobi_t h, const double* u0, bool warm, double tol, int32_t max_it
   return fail(HOBI_ERR_NOT_CONVERGED, "GMRES did not reach tol within max_it iterations (rel residual " +
                                           std::to_string(fs.rel) + ")");
 }
+
+// Mixed-precision solve (iterative refinement): the correction equation A d = r is solved by
+// FP32-bulk GMRES to 1e-6, the residual r = b - A u of the accumulated u is formed with the FP64
+// far field, until ||r|| / ||b|| <= tol on the FP64 operator.
+int solve_refined_impl(hobi_t h, double tol, int32_t max_refine, int32_t max_it, double* phi, double* dphi,
+                       hobi_solve_info* info) {
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (!(tol > 0.0) || max_refine < 1 || max_it < 1)
+    return fail(HOBI_ERR_ARG, "need tol > 0, max_refine >= 1 and max_it >= 1");
+  DeviceGuard guard(h->device);
+  const int64_t n = 2 * h->nv;
+  if (!h->ref_x) {
+    HOBI_TRY(h->alloc(&h->ref_x, n));
+    HOBI_TRY(h->alloc(&h->ref_r, n));
+    HOBI_TRY(h->alloc(&h->ref_d, n));
+    HOBI_TRY(h->alloc(&h->ref_scal, 1));
+    HOBI_CK(cudaEventCreate(&h->ref_t0));
+    HOBI_CK(cudaEventCreate(&h->ref_t1));
+  }
+  HOBI_TRY(h->enter());
+  HOBI_CK(cudaEventRecord(h->ref_t0, h->stream));
+  auto norm = [&](const double* v, double* out) -> int {
+    HOBI_CK(launch_norm2(v, n, h->ref_scal, h->stream));
+    HOBI_CK(cudaMemcpyAsync(out, h->ref_scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    HOBI_CK(cudaStreamSynchronize(h->stream));
+    h->launches += 1;
+    return HOBI_OK;
+  };
+  const int saved = h->precision;
+  double bnorm = 0.0, rel = 0.0;
+  HOBI_CK(cudaMemsetAsync(h->ref_x, 0, sizeof(double) * n, h->stream));
+  HOBI_TRY(norm(h->b, &bnorm));
+  std::vector<double> hist;
+  int inner_it = 0, status = HOBI_OK;
+  double pairs = 0.0;
+  for (int k = 0; bnorm > 0.0; ++k) {
+    if (k == 0) {
+      HOBI_CK(cudaMemcpyAsync(h->ref_r, h->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    } else {  // r = b - A u with the FP64 far field
+      h->precision = HOBI_FP64;
+      HOBI_TRY(h->matvec_dev(h->ref_x, nullptr, 0, h->w));
+      HOBI_CK(launch_residual_start(h->b, h->w, h->ref_r, n, h->stream));
+      h->launches += 1;
+      pairs += (double)h->nv * (double)h->n_nodes;
+    }
+    double rnorm = 0.0;
+    HOBI_TRY(norm(h->ref_r, &rnorm));
+    rel = rnorm / bnorm;
+    hist.push_back(rel);
+    if (rel <= tol || k >= max_refine) break;
+    // FP32-bulk GMRES on A d = r (b and x of the handle point at r and d meanwhile)
+    h->precision = HOBI_FP32_BULK;
+    std::swap(h->b, h->ref_r);
+    std::swap(h->x, h->ref_d);
+    hobi_solve_info ii;
+    memset(&ii, 0, sizeof ii);
+    const int r = solve_impl(h, nullptr, false, 1e-6, max_it, nullptr, nullptr, &ii);
+    std::swap(h->b, h->ref_r);
+    std::swap(h->x, h->ref_d);
+    h->precision = saved;
+    inner_it += ii.iterations;
+    pairs += ii.farfield_pairs;
+    if (r != HOBI_OK && r != HOBI_ERR_NOT_CONVERGED) return r;
+    HOBI_CK(launch_add_in_place(h->ref_x, h->ref_d, n, h->stream));
+    h->launches += 1;
+  }
+  h->precision = saved;
+  HOBI_CK(cudaMemcpyAsync(h->x, h->ref_x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  HOBI_CK(cudaEventRecord(h->ref_t1, h->stream));
+  if (phi) HOBI_TRY(h->copy_out(phi, h->x, h->nv));
+  if (dphi) HOBI_TRY(h->copy_out(dphi, h->x + h->nv, h->nv));
+  HOBI_TRY(h->finish());
+  HOBI_CK(cudaEventSynchronize(h->ref_t1));
+  h->have_solution = true;
+  if (rel > tol) status = fail(HOBI_ERR_NOT_CONVERGED, "refinement did not reach tol within max_refine steps "
+                                                       "(FP64 rel residual " + std::to_string(rel) + ")");
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ref_t0, h->ref_t1);
+    info->iterations = inner_it;
+    info->converged = rel <= tol;
+    info->rel_residual = rel;
+    info->solve_ms = ms;
+    info->farfield_pairs = pairs;
+    if (info->resid_history && info->resid_capacity > 0) {
+      const int cnt = (int)hist.size() < info->resid_capacity ? (int)hist.size() : info->resid_capacity;
+      for (int i = 0; i < cnt; ++i) info->resid_history[i] = hist[i];
+    }
+  }
+  return status;
+}
 }  // namespace
 
 extern "C" {
@@ -987,6 +1084,12 @@ extern "C" {
 int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, hobi_solve_info* info) {
   NvtxRange nvtx_range("hobi_solve");
   return solve_impl(h, nullptr, false, tol, max_it, phi, dphi, info);
+}
+
+int hobi_solve_refined(hobi_t h, double tol, int32_t max_refine, int32_t max_it, double* phi, double* dphi,
+                       hobi_solve_info* info) {
+  NvtxRange nvtx_range("hobi_solve_refined");
+  return solve_refined_impl(h, tol, max_refine, max_it, phi, dphi, info);
 }
 
 int hobi_solve_from(hobi_t h, const double* u0, double tol, int32_t max_it, double* phi, double* dphi,

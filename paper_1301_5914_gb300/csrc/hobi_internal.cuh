@@ -175,6 +175,9 @@ cudaError_t launch_cycle_start(double* Vb, int64_t n, const double* nrm2, GmresS
 cudaError_t launch_finish_cycle(const double* H, int m, const double* g, const GmresState* st, double* y,
                                 const double* Vb, int64_t ld, double* x, int64_t n, cudaStream_t s);
 cudaError_t launch_residual_start(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t s);
+// mixed-precision refinement: x += d; out[0] = ||v||_2 (device scalar)
+cudaError_t launch_add_in_place(double* x, const double* d, int64_t n, cudaStream_t s);
+cudaError_t launch_norm2(const double* v, int64_t n, double* out, cudaStream_t s);
 
 
 // ---- batched solve (k_batch.cu) ----

@@ -167,6 +167,20 @@ __global__ void k_residual(const double* __restrict__ b, const double* __restric
     r[i] = b[i] - Ax[i];
 }
 
+// x += d (mixed-precision refinement)
+__global__ void k_add_in_place(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+
+// out[0] = ||v||_2, one block, fixed summation order
+__global__ void k_norm2(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * v[i];
+  s = block_reduce(s);
+  if (threadIdx.x == 0) out[0] = sqrt(s);
+}
+
 inline int grid_for(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -218,6 +232,16 @@ cudaError_t launch_finish_cycle(const double* H, int m, const double* g, const G
                                 const double* Vb, int64_t ld, double* x, int64_t n, cudaStream_t s) {
   k_backsolve<<<1, 32, 0, s>>>(H, m, g, st, y);
   k_update_x<<<grid_for(n), kThreads, 0, s>>>(Vb, ld, y, st, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_in_place(double* x, const double* d, int64_t n, cudaStream_t s) {
+  k_add_in_place<<<grid_for(n), kThreads, 0, s>>>(x, d, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(const double* v, int64_t n, double* out, cudaStream_t s) {
+  k_norm2<<<1, kThreads, 0, s>>>(v, n, out);
   return cudaGetLastError();
 }
 

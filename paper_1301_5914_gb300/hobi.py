@@ -34,7 +34,7 @@ KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
 
 EXPORTS = [
     "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
-    "hobi_solve", "hobi_solve_from", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
+    "hobi_solve", "hobi_solve_from", "hobi_solve_refined", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
     "hobi_reaction_potential_noalloc", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
     "hobi_fast_info",
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_rhs.argtypes = [vp, dp]
     lib.hobi_solve.argtypes = [vp, C.c_double, C.c_int32, dp, dp, C.POINTER(SolveInfo)]
     lib.hobi_solve_from.argtypes = [vp, dp, C.c_double, C.c_int32, dp, dp, C.POINTER(SolveInfo)]
+    lib.hobi_solve_refined.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, dp, dp, C.POINTER(SolveInfo)]
     lib.hobi_set_solution.argtypes = [vp, dp]
     lib.hobi_get_solution.argtypes = [vp, dp]
     lib.hobi_reaction_potential.argtypes = [vp, dp, i64, dp]
@@ -97,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(C.c_double)]
     lib.hobi_kernel_launches.argtypes = [vp, C.POINTER(i64)]
     lib.hobi_plan_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.hobi_fast_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)]
     lib.hobi_destroy.argtypes = [vp]
     lib.hobi_destroy.restype = None
     lib.hobi_setup_batch.argtypes = [C.c_int32, dp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
@@ -279,6 +282,28 @@ class Solver:
              "rel_residual": info.rel_residual, "solve_ms": info.solve_ms, "farfield_pairs": info.farfield_pairs}
         if hist is not None:
             d["history"] = np.array(hist[: min(history, info.iterations + 1)])
+        return phi, dphi, d
+
+    def solve_refined(self, tol: float = 1e-10, max_refine: int = 8, max_it: int = 200, history: int = 0,
+                      raise_on_fail: bool = True):
+        """Mixed-precision solve (hobi_solve_refined): FP32-bulk GMRES corrections, FP64 residuals,
+        until ||b - A u|| / ||b|| <= tol on the FP64 operator. Returns (phi, dphi, info)."""
+        phi = self._out(self.npts)
+        dphi = self._out(self.npts)
+        info = SolveInfo()
+        hist = None
+        if history > 0:
+            hist = (C.c_double * history)()
+            info.resid_history = C.cast(hist, C.POINTER(C.c_double))
+            info.resid_capacity = history
+        code = self._lib.hobi_solve_refined(self._h, float(tol), int(max_refine), int(max_it), self._ptr(phi),
+                                            self._ptr(dphi), C.byref(info))
+        if raise_on_fail and code != HOBI_OK:
+            _check(code)
+        d = {"status": code, "iterations": info.iterations, "converged": bool(info.converged),
+             "rel_residual": info.rel_residual, "solve_ms": info.solve_ms, "farfield_pairs": info.farfield_pairs}
+        if hist is not None:
+            d["history"] = np.array(hist[: min(history, max_refine + 1)])
         return phi, dphi, d
 
     def set_solution(self, u):
