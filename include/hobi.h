@@ -249,6 +249,13 @@ int hobi_plan_info(hobi_t h, int32_t* shape, int32_t* chunks, int32_t* tuned);
 int hobi_fast_info(hobi_t h, int64_t* direct_pairs, int64_t* approx_pairs, int32_t* batches,
                    int32_t* proxy_clusters, int32_t* tasks);
 
+/* The same statistics for a treecode plan built on the host from given FP64 points, without a
+ * handle or a GPU: nodes [n_nodes][3] (sources), targets [n_targets][3], both host arrays. Plan
+ * inspection for callers choosing degree and theta before a setup. */
+int hobi_fast_plan_stats(const double* nodes, int64_t n_nodes, const double* targets, int64_t n_targets,
+                         int32_t degree, double theta, int64_t* direct_pairs, int64_t* approx_pairs,
+                         int32_t* batches, int32_t* proxy_clusters);
+
 /* Free every resource of the handle (NULL is a no-op). */
 void hobi_destroy(hobi_t h);
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <stdio.h>
 #include <stdlib.h>
@@ -1221,6 +1222,23 @@ int hobi_fast_info(hobi_t h, int64_t* direct_pairs, int64_t* approx_pairs, int32
   if (batches) *batches = h->fast_batches;
   if (proxy_clusters) *proxy_clusters = h->fast_npc;
   if (tasks) *tasks = h->fast_ntasks;
+  return HOBI_OK;
+}
+
+int hobi_fast_plan_stats(const double* nodes, int64_t n_nodes, const double* targets, int64_t n_targets,
+                         int32_t degree, double theta, int64_t* direct_pairs, int64_t* approx_pairs,
+                         int32_t* batches, int32_t* proxy_clusters) {
+  if (!nodes || !targets || n_nodes < 1 || n_targets < 1) return fail(HOBI_ERR_ARG, "need nodes and targets");
+  if (n_nodes > INT32_MAX / 2 || n_targets > INT32_MAX / 2) return fail(HOBI_ERR_ARG, "too many points");
+  if (degree < 2 || degree > kFastMaxDegree) return fail(HOBI_ERR_ARG, "degree must be 2..10");
+  if (!(theta > 0.0 && theta <= 1.0)) return fail(HOBI_ERR_ARG, "theta must be in (0, 1]");
+  FastPlanHost P;
+  const double origin[3] = {0.0, 0.0, 0.0};
+  build_fast_plan(nodes, (int)n_nodes, targets, (int)n_targets, origin, 1.0, degree, theta, 1, 0, &P);
+  if (direct_pairs) *direct_pairs = P.direct_pairs;
+  if (approx_pairs) *approx_pairs = P.approx_pairs;
+  if (batches) *batches = (int32_t)P.batch.size();
+  if (proxy_clusters) *proxy_clusters = (int32_t)P.pc_offset.size();
   return HOBI_OK;
 }
 
