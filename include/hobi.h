@@ -233,8 +233,8 @@ int hobi_profile_read(hobi_t h, double* farfield_ms, int64_t* launches, double* 
  * a replayed GMRES graph counts each of its kernels). */
 int hobi_kernel_launches(hobi_t h, int64_t* n);
 
-/* The FP32 far-field launch plan of the matvec: block shape index (0: 128 threads x 8 targets,
- * 256-node tiles; 1: 64 x 8, 128; 2: 32 x 8, 64; 3: 32 x 4, 64), source chunks, and whether
+/* The FP32 far-field launch plan of the matvec: block shape index (0: 32 threads x 8 targets,
+ * 128-node tiles; 1: 64 x 8, 128; 2: 32 x 8, 64; 3: 32 x 4, 64), source chunks, and whether
  * the shape was measured by the autotuner (1) or chosen analytically (0). */
 int hobi_plan_info(hobi_t h, int32_t* shape, int32_t* chunks, int32_t* tuned);
 

@@ -480,8 +480,8 @@ namespace {
 // Analytic shape choice: the largest block shape that still yields enough independent
 // (target block, source tile) work items to fill the machine several times over.
 int choose_shape(int n_targets, int n_pad, int num_sms) {
-  static const int per_block[kNumFF32Shapes] = {1024, 512, 256, 128};
-  static const int tile[kNumFF32Shapes] = {256, 128, 64, 64};
+  static const int per_block[kNumFF32Shapes] = {256, 512, 256, 128};
+  static const int tile[kNumFF32Shapes] = {128, 128, 64, 64};
   for (int s = 0; s < kNumFF32Shapes; ++s) {
     long tt = (n_targets + per_block[s] - 1) / per_block[s];
     long tiles = n_pad / tile[s];

@@ -27,10 +27,11 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kInv4Pi = 1.0 / (4.0 * 3.14159265358979323846);
 constexpr double kCoulomb = 332.0716;  // kcal A / (mol e^2)
 
-// Far-field tiling (FP32): threads per block, targets per thread, source nodes per smem tile.
-// 8 targets per thread (4 packed pairs) with 2 blocks of 128 threads per SM: fewer warps, but
-// more independent pair chains per warp, which hides the MUFU and FMA latencies better.
-constexpr int kFF32Threads = 128;
+// Far-field tiling (FP32): targets per thread and the FP64 / padding tile. 8 targets per thread
+// (4 packed pairs) with 8 warps per SM: fewer warps than 2 targets per thread would allow, but
+// more independent pair chains per warp, which hides the MUFU and FMA latencies better. The
+// block shapes of the single-molecule kernel are listed below (kNumFF32Shapes).
+constexpr int kFF32Threads = 32;
 constexpr int kFF32Targets = 8;
 constexpr int kTile = 256;
 // FP64 path
@@ -114,9 +115,9 @@ cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const do
                           cudaStream_t s, const int* pos = nullptr);
 cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* src64, cudaStream_t s);
 
-// FP32 far-field block shapes (threads, targets per thread, source tile): 0 = 128 x 8, tile 256;
-// 1 = 64 x 8, tile 128; 2 = 32 x 8, tile 64; 3 = 32 x 4, tile 64 (small problems). Targets per
-// block: 1024, 512, 256, 128.
+// FP32 far-field block shapes (threads, targets per thread, source tile): 0 = 32 x 8, tile 128
+// (one warp, 8 blocks per SM); 1 = 64 x 8, tile 128; 2 = 32 x 8, tile 64; 3 = 32 x 4, tile 64
+// (small problems). Targets per block: 256, 512, 256, 128.
 constexpr int kNumFF32Shapes = 4;
 struct FarFieldPlan {
   int n_targets;

@@ -16,8 +16,9 @@
 // FP32-bulk kernel: each thread keeps 8 targets in registers as four packed pairs and evaluates
 // every pair formula with Blackwell's paired FP32 instructions (__ffma2_rn / __fmul2_rn /
 // __fadd2_rn: one instruction = the same operation on two targets), which halves the issue
-// slots of the FMA-pipe work so that the FMA pipe itself becomes the limit. 256-node source
-// tiles are staged in shared memory, each source value stored twice ({v, v}) so one LDS.128
+// slots of the FMA-pipe work so that the FMA pipe itself becomes the limit. Source tiles (128
+// nodes in the default one-warp shape) are staged in shared memory by bulk asynchronous copies,
+// each source value stored twice ({v, v}) so one LDS.128
 // feeds two packed operands; rsqrt and exp2 go to the MUFU pipe (rsqrt.approx / ex2.approx).
 // Each tile's FP32 sum is folded into a compensated (two-float) accumulator, and the result is
 // written as FP64 per (source chunk, target); the combine kernel adds the chunks in a fixed order.
@@ -187,7 +188,7 @@ cudaError_t launch_pad_sources(int n_nodes, int n_pad, float4* src32, double* sr
 struct FF32Shape {
   int nt, tp, tile;
 };
-constexpr FF32Shape kShapes[kNumFF32Shapes] = {{128, 4, 256}, {64, 4, 128}, {32, 4, 64}, {32, 2, 64}};
+constexpr FF32Shape kShapes[kNumFF32Shapes] = {{32, 4, 128}, {64, 4, 128}, {32, 4, 64}, {32, 2, 64}};
 
 template <bool ROW2, bool KS, bool SKIP>
 cudaError_t launch32_shape(int shape, dim3 grid, const float4* tgt, int nt, const float4* src, int n_tiles, int tpc,
@@ -203,7 +204,7 @@ cudaError_t launch32_shape(int shape, dim3 grid, const float4* tgt, int nt, cons
       k_farfield32<ROW2, KS, SKIP, 32, 2, 64><<<grid, 32, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
       break;
     default:
-      k_farfield32<ROW2, KS, SKIP, 128, 4, 256><<<grid, 128, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
+      k_farfield32<ROW2, KS, SKIP, 32, 4, 128><<<grid, 32, 0, s>>>(tgt, nt, src, n_tiles, tpc, cs, part, ldp, err);
   }
   return cudaGetLastError();
 }
@@ -222,7 +223,7 @@ int occupancy32(int shape) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 32, 2, 64>, 32, 0);
       break;
     default:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 128, 4, 256>, 128, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield32<ROW2, true, SKIP, 32, 4, 128>, 32, 0);
   }
   return n > 0 ? n : 1;
 }
