@@ -490,6 +490,8 @@ int choose_shape(int n_targets, int n_pad, int num_sms) {
   return kNumFF32Shapes - 1;
 }
 
+constexpr int kTuneLaunches = 4;  // per candidate shape: one warm-up, then the fastest of three
+
 // Autotuner decisions, per process (and optionally in a file): key -> shape
 std::mutex g_tune_mu;
 std::vector<std::pair<std::string, int>> g_tune;
@@ -680,7 +682,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
       float best = 1e30f;
       for (int sh = 0; sh < kNumFF32Shapes; ++sh) {
         float t = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
+        for (int rep = 0; rep < kTuneLaunches; ++rep) {
           HOBI_CK(cudaEventRecord(h->ev_t0, h->stream));
           HOBI_CK(launch_farfield(true, cand[sh], h->tgt32, h->tgt64, h->src32, h->src64, h->eps, h->kappa, h->part,
                                   h->ff_err, h->stream, skip));
@@ -688,9 +690,9 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
           HOBI_CK(cudaEventSynchronize(h->ev_t1));
           float ms = 0.f;
           HOBI_CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
-          if (rep > 0) t = std::min(t, ms);  // the first launch warms up
+          if (rep > 0) t = std::min(t, ms);  // the first launch warms up; the fastest of the rest
         }
-        h->launches += 2;
+        h->launches += kTuneLaunches;
         if (t < best * 0.98f) {  // prefer the earlier (larger) shape unless clearly faster
           best = t;
           shape = sh;
