@@ -261,7 +261,7 @@ void hobi_destroy(hobi_t h);
 
 /* ---------------------------------------------------------------------------------------
  * Batched solve: many molecules (same eps1, eps2, kappa) solved together. Every GMRES step
- * runs one persistent far-field launch over a task list covering every unconverged molecule,
+ * runs one far-field launch over a task list covering every unconverged molecule,
  * and the Arnoldi/Givens work of all molecules in one set of launches (replayed as a CUDA
  * graph); converged molecules drop out. Each molecule follows exactly the single-molecule
  * method above (Sec. 2.2-2.3, Eqs. eqdbef3-eqdbef6), with its own Krylov space, residual

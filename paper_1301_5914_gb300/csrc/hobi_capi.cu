@@ -81,11 +81,11 @@ struct hobi_ctx {
   double xs = 1;            // coordinate scale of the FP32 tables (ff32_coord_scale(kappa))
   int num_sms = 1;
   // fast summation (treecode) of the FP32 far field; fast_degree 0: direct summation
-  int fast_degree = 0, fast_chunks = 1, fast_ntasks = 0, fast_nup = 0, fast_npc = 0, fast_grid = 1;
+  int fast_degree = 0, fast_chunks = 1, fast_ntasks = 0, fast_nup = 0, fast_npc = 0, fast_resident = 1;
   int fast_batches = 0, fast_nseg = 0;
   double fast_theta = 0.7;
   int64_t fast_direct_pairs = 0, fast_approx_pairs = 0;
-  int *fast_pos = nullptr, *fast_tmap = nullptr, *fast_pcoff = nullptr, *fast_counter = nullptr;
+  int *fast_pos = nullptr, *fast_tmap = nullptr, *fast_pcoff = nullptr;
   int2 *fast_batch = nullptr, *fast_seg = nullptr, *fast_pcitems = nullptr;
   FastTask* fast_tasks = nullptr;
   FastUpItem* fast_up = nullptr;
@@ -215,8 +215,8 @@ struct hobi_ctx {
     }
     HOBI_CK(launch_fast_upward(fast_nup, fast_up, fast_axes, fast_half, fast_src, fast_degree, fast_partial, fast_npc,
                                fast_pcitems, fast_pcoff, eps, stream));
-    HOBI_CK(launch_fast_eval(fast_tasks, fast_ntasks, fast_counter, fast_batch, fast_seg, fast_src, fast_tgt,
-                             fast_tmap, (int)nv, eps, kappa, out, fast_grid, ff_err, stream));
+    HOBI_CK(launch_fast_eval(fast_tasks, fast_ntasks, fast_batch, fast_seg, fast_src, fast_tgt, fast_tmap, (int)nv,
+                             eps, kappa, out, ff_err, stream));
     return HOBI_OK;
   }
   int farfield(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, double* out,
@@ -281,9 +281,9 @@ struct hobi_ctx {
     HOBI_CK(cudaMemcpyAsync(hx.data(), V, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost, stream));
     HOBI_CK(cudaMemcpyAsync(hc.data(), center, sizeof(double) * 3, cudaMemcpyDeviceToHost, stream));
     HOBI_CK(cudaStreamSynchronize(stream));
-    fast_grid = num_sms * fast_eval_blocks_per_sm(kappa);
+    fast_resident = num_sms * fast_eval_blocks_per_sm(kappa);  // evaluation blocks resident at once
     FastPlanHost P;
-    build_fast_plan(hy.data(), (int)n_nodes, hx.data(), (int)nv, hc.data(), xs, fast_degree, fast_theta, fast_grid,
+    build_fast_plan(hy.data(), (int)n_nodes, hx.data(), (int)nv, hc.data(), xs, fast_degree, fast_theta, fast_resident,
                     piece_sources, &P);
     const int n3 = (fast_degree + 1) * (fast_degree + 1) * (fast_degree + 1);
     fast_chunks = P.chunks;
@@ -315,7 +315,6 @@ struct hobi_ctx {
     HOBI_TRY(alloc(&fast_src, 4 * (size_t)P.n_entries));
     HOBI_TRY(alloc(&fast_tgt, 2 * (size_t)nv));
     HOBI_TRY(alloc(&fast_partial, (size_t)fast_nup * n3));
-    HOBI_TRY(alloc(&fast_counter, 1));
     HOBI_CK(launch_fast_targets((int)nv, fast_tmap, tgt32, fast_tgt, stream));
     launches += 1;
     HOBI_CK(cudaStreamSynchronize(stream));  // the host vectors above are released on return

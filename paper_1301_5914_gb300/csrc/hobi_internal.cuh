@@ -211,7 +211,7 @@ struct MolDesc {          // one molecule's device tables (owned by its single-m
   const int2* fpcitems;
   const int* fpcoff;
 };
-struct FFTask {           // one persistent far-field work item: targets of block bx, tiles [t0, t1)
+struct FFTask {           // one batched far-field work item: targets of block bx, tiles [t0, t1)
   int mol, bx, t0, t1, chunk;
   int fast;               // 1: treecode task, bx = batch, [t0, t1) = segments of the molecule's list
 };
@@ -231,7 +231,7 @@ struct MolState {
 };
 constexpr int kSegLen = 4096;
 constexpr int kTilesPerTask = 16;  // kTile-node tiles per task (FP64), i.e. 4096 source nodes
-// Batched FP32 far field: one-warp persistent blocks with 8 targets per thread (256 targets per
+// Batched FP32 far field: one one-warp block per task, 8 targets per thread (256 targets per
 // task, so a molecule wastes at most 255 target slots) and 128-node tiles, 32 of them per task
 // (the same 4096 source nodes per chunk as the FP64 tasks).
 constexpr int kBatchFF32Threads = 32;
@@ -279,9 +279,9 @@ cudaError_t launch_fast_targets(int nv, const int* tmap, const float4* tgt32, fl
 cudaError_t launch_fast_upward(int nup, const FastUpItem* items, const float* axes, const float* half,
                                float4* srcf, int degree, float4* partial, int npc, const int2* pc_items,
                                const int* pc_off, double eps, cudaStream_t s);
-cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, int* counter, const int2* batch, const int2* seg,
-                             const float4* srcf, const float4* tgtf, const int* tmap, int nv, double eps,
-                             double kappa, double* part, int grid, int* err, cudaStream_t s);
+cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, const int2* batch, const int2* seg, const float4* srcf,
+                             const float4* tgtf, const int* tmap, int nv, double eps, double kappa, double* part,
+                             int* err, cudaStream_t s);
 int fast_eval_blocks_per_sm(double kappa);
 // batched treecode upward pass: work items and proxy clusters of every fast molecule
 struct FastUpItemB {
@@ -296,6 +296,7 @@ cudaError_t launch_fast_upward_batch(int nitems, const FastUpItemB* items, int n
 
 cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const int64_t* node_off, int64_t total_nodes,
                                 const double* u, const int* kptr, int64_t ld, const MolState* ms, cudaStream_t s);
+// FP32: one block per task; FP64: `grid` persistent blocks sharing the task counter `counter`
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,
                                   const MolState* ms, double eps, double kappa, int grid, int* err, cudaStream_t s);
 int farfield_batch_blocks_per_sm(bool fp32, double kappa);

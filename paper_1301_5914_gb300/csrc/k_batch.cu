@@ -65,45 +65,39 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
     ff::gather64_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, d.src64);
 }
 
-// Persistent far field: blocks pull tasks (molecule, target block, source tiles [t0, t1), chunk)
-// from an atomic counter (reset to 0 before each launch) until the list is exhausted; tasks of
-// converged molecules are skipped. Each task writes its own partial slot, so the result does not
-// depend on which block ran which task.
+// Batched FP32 far field: one one-warp block per task (molecule, target block, source tiles
+// [t0, t1) or treecode piece, chunk); blocks of converged molecules return at once. The task list
+// is sorted longest first and blocks are dispatched in index order, so the long tasks start first.
+// Each task writes its own partial slot, so the result does not depend on the schedule. (A
+// persistent form, blocks pulling tasks from an atomic counter, measured 4.5 % slower.)
 template <bool KS>
 __global__ void __launch_bounds__(kBatchFF32Threads, 8)
-    k_farfield_batch32(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, int ntasks, int* counter,
-                       const MolState* ms, FF32Consts cs, int* err) {
+    k_farfield_batch32(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, const MolState* ms,
+                       FF32Consts cs, int* err) {
   constexpr int kStage = kFastSeg > kBatchFF32Tile ? kFastSeg : kBatchFF32Tile;  // entries per stage
   __shared__ __align__(128) float4 sh[2 * 4 * kStage];
   __shared__ __align__(8) unsigned long long bars[2];
-  __shared__ int s_task;
   if (threadIdx.x == 0) ff::tile_barriers_init(bars);
   __syncthreads();
-  uint32_t phases = 0;  // barrier parities, carried from task to task
-  for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
-    __syncthreads();
-    const int t = s_task;
-    __syncthreads();
-    if (t >= ntasks) break;
-    const FFTask tk = tasks[t];
-    if (mol_done(ms, tk.mol)) continue;
-    const MolDesc& d = mols[tk.mol];
-    double* out = d.part + (size_t)tk.chunk * 2 * d.nv;
-    bool ok;
-    if (tk.fast) {  // treecode task: a piece of a batch's segment list (direct leaves and proxies)
-      const int2 b = d.fbatch[tk.bx];
-      const ff::SegmentTiles tiles{d.fsrc, d.fseg + tk.t0};
-      ok = ff::ff32_core<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kFastSeg>(
-          d.ftgt, b.x, b.x + b.y, d.ftmap, d.nv, tiles, tk.t1 - tk.t0, cs, out, sh, bars, phases, err);
-    } else {
-      ok = ff::ff32_block<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kBatchFF32Tile>(
-          d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs, out, tk.bx, sh, bars, phases, err);
-    }
-    if (!ok) return;  // the tile pipeline timed out (reported through err)
+  uint32_t phases = 0;
+  const FFTask tk = tasks[blockIdx.x];
+  if (mol_done(ms, tk.mol)) return;
+  const MolDesc& d = mols[tk.mol];
+  double* out = d.part + (size_t)tk.chunk * 2 * d.nv;
+  // a timed-out tile pipeline is reported through err
+  if (tk.fast) {  // treecode task: a piece of a batch's segment list (direct leaves and proxies)
+    const int2 b = d.fbatch[tk.bx];
+    const ff::SegmentTiles tiles{d.fsrc, d.fseg + tk.t0};
+    ff::ff32_core<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kFastSeg>(
+        d.ftgt, b.x, b.x + b.y, d.ftmap, d.nv, tiles, tk.t1 - tk.t0, cs, out, sh, bars, phases, err);
+  } else {
+    ff::ff32_block<true, KS, false, kBatchFF32Threads, kFF32Targets / 2, kBatchFF32Tile>(
+        d.tgt32, d.nv, d.src32, tk.t0, tk.t1, cs, out, tk.bx, sh, bars, phases, err);
   }
 }
 
+// Batched FP64 far field: persistent blocks pull tasks from an atomic counter (reset to 0 before
+// each launch) until the list is exhausted; tasks of converged molecules are skipped.
 __global__ void __launch_bounds__(kFF64Threads)
     k_farfield_batch64(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, int ntasks, int* counter,
                        const MolState* ms, double kap, double eps) {
@@ -329,15 +323,16 @@ cudaError_t launch_gather_batch(bool fp32, const MolDesc* mols, int nmol, const 
 
 cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* tasks, int ntasks, int* counter,
                                   const MolState* ms, double eps, double kappa, int grid, int* err, cudaStream_t s) {
-  cudaMemsetAsync(counter, 0, sizeof(int), s);
-  if (fp32 && ff32_kappa_scaled(kappa))
-    k_farfield_batch32<true><<<grid, kBatchFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
-                                                          err);
-  else if (fp32)
-    k_farfield_batch32<false><<<grid, kBatchFF32Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff32_consts(eps, kappa),
-                                                           err);
-  else
+  if (ntasks <= 0) return cudaSuccess;
+  if (fp32 && ff32_kappa_scaled(kappa)) {
+    k_farfield_batch32<true><<<ntasks, kBatchFF32Threads, 0, s>>>(mols, tasks, ms, ff32_consts(eps, kappa), err);
+  } else if (fp32) {
+    k_farfield_batch32<false><<<ntasks, kBatchFF32Threads, 0, s>>>(mols, tasks, ms, ff32_consts(eps, kappa), err);
+  } else {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
     k_farfield_batch64<<<grid, kFF64Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, kappa, eps);
+  }
   return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@
 // r_B + r_C < theta |c_B - c_C| is approximated, a leaf otherwise summed directly, an inner
 // cluster opened. Each batch's segment list is cut into `chunks` pieces of equal work.
 // Per matvec: the gather writes the node densities in tree order, the upward kernels form the
-// proxy densities, and a persistent kernel evaluates (batch, piece) tasks into per-piece partial
+// proxy densities, and one block per (batch, piece) task evaluates it into the piece's partial
 // rows, which the usual combine kernel adds up with the singular correction.
 #include <math.h>
 
@@ -453,33 +453,26 @@ __global__ void k_fast_finish_batch(int npcs, const FastPCB* __restrict__ pcs, c
   finish_entry(e.pc, (int)(g % n3), d.fpcitems, d.fpcoff, d.faxes, d.fpartial, n1, one_minus_eps, d.fsrc);
 }
 
-// Persistent evaluation: one-warp blocks pull (batch, piece) tasks from an atomic counter and
-// run the far-field block over the piece's segments into the piece's partial rows.
+// Evaluation: one one-warp block per (batch, piece) task, running the far-field block over the
+// piece's segments into the piece's partial rows. The plan lists tasks longest first and blocks
+// are dispatched in index order, so the long tasks start first. (A persistent form, blocks pulling
+// tasks from an atomic counter, measured 7 % slower with the same arithmetic.)
 template <bool KS>
 __global__ void __launch_bounds__(kFastThreads, 8)
-    k_fast_eval(const FastTask* __restrict__ tasks, int ntasks, int* counter, const int2* __restrict__ batch,
-                const int2* __restrict__ seg, const float4* __restrict__ srcf, const float4* __restrict__ tgtf,
-                const int* __restrict__ tmap, int nv, FF32Consts cs, double* __restrict__ part, int* err) {
+    k_fast_eval(const FastTask* __restrict__ tasks, const int2* __restrict__ batch, const int2* __restrict__ seg,
+                const float4* __restrict__ srcf, const float4* __restrict__ tgtf, const int* __restrict__ tmap,
+                int nv, FF32Consts cs, double* __restrict__ part, int* err) {
   __shared__ __align__(128) float4 sh[2 * 4 * kFastSeg];
   __shared__ __align__(8) unsigned long long bars[2];
-  __shared__ int s_task;
   if (threadIdx.x == 0) ff::tile_barriers_init(bars);
   __syncthreads();
   uint32_t phases = 0;
-  for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
-    __syncthreads();
-    const int t = s_task;
-    __syncthreads();
-    if (t >= ntasks) break;
-    const FastTask tk = tasks[t];
-    const int2 b = batch[tk.batch];
-    const ff::SegmentTiles tiles{srcf, seg + tk.s0};
-    const bool ok = ff::ff32_core<true, KS, false, kFastThreads, kFF32Targets / 2, kFastSeg>(
-        tgtf, b.x, b.x + b.y, tmap, nv, tiles, tk.s1 - tk.s0, cs, part + (size_t)tk.chunk * 2 * nv, sh, bars,
-        phases, err);
-    if (!ok) return;  // the tile pipeline timed out (reported through err)
-  }
+  const FastTask tk = tasks[blockIdx.x];
+  const int2 b = batch[tk.batch];
+  const ff::SegmentTiles tiles{srcf, seg + tk.s0};
+  ff::ff32_core<true, KS, false, kFastThreads, kFF32Targets / 2, kFastSeg>(
+      tgtf, b.x, b.x + b.y, tmap, nv, tiles, tk.s1 - tk.s0, cs, part + (size_t)tk.chunk * 2 * nv, sh, bars, phases,
+      err);  // a timed-out tile pipeline is reported through err
 }
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -521,18 +514,15 @@ cudaError_t launch_fast_upward(int nup, const FastUpItem* items, const float* ax
   return cudaGetLastError();
 }
 
-cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, int* counter, const int2* batch, const int2* seg,
-                             const float4* srcf, const float4* tgtf, const int* tmap, int nv, double eps,
-                             double kappa, double* part, int grid, int* err, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
+cudaError_t launch_fast_eval(const FastTask* tasks, int ntasks, const int2* batch, const int2* seg, const float4* srcf,
+                             const float4* tgtf, const int* tmap, int nv, double eps, double kappa, double* part,
+                             int* err, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
   const FF32Consts cs = ff32_consts(eps, kappa);
   if (ff32_kappa_scaled(kappa))
-    k_fast_eval<true><<<grid, kFastThreads, 0, s>>>(tasks, ntasks, counter, batch, seg, srcf, tgtf, tmap, nv, cs,
-                                                     part, err);
+    k_fast_eval<true><<<ntasks, kFastThreads, 0, s>>>(tasks, batch, seg, srcf, tgtf, tmap, nv, cs, part, err);
   else
-    k_fast_eval<false><<<grid, kFastThreads, 0, s>>>(tasks, ntasks, counter, batch, seg, srcf, tgtf, tmap, nv, cs,
-                                                      part, err);
+    k_fast_eval<false><<<ntasks, kFastThreads, 0, s>>>(tasks, batch, seg, srcf, tgtf, tmap, nv, cs, part, err);
   return cudaGetLastError();
 }
 
