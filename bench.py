@@ -481,15 +481,6 @@ def run_ours(args):
                 acc["E_rel_fp32_vs_fp64_max"] = float(np.max(np.abs(E32 - E64) / np.abs(E64)))
             else:
                 acc.update(E_sol_fp32=E32, E_sol_fp64=E64, E_rel_fp32_vs_fp64=abs(E32 - E64) / abs(E64))
-                if args.workload == "c2l6":
-                    try:
-                        from oracle import kirkwood as kw
-
-                        e_ex = kw.solvation_energy(Qh, 10.0, e1, e2, ka)
-                        acc["E_sol_kirkwood"] = e_ex
-                        acc["E_rel_fp64_vs_kirkwood"] = abs(E64 - e_ex) / abs(e_ex)
-                    except ImportError:
-                        pass
         # phases of one step, outside the timed region (CUDA events on the library's stream order)
         phases = step_phases(make, batched, tol, stream) if not batched else None
         # fast summation (treecode, beyond the paper) on the same inputs, outside the timed region:

@@ -59,3 +59,33 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             hobi.load_library(str(tmp_path / "missing" / "libhobi.so"))
     finally:
         hobi._lib = saved
+
+
+def _oracle_imports_by_function(path):
+    """(enclosing top-level function or None, line) of every import of the oracle package."""
+    tree = ast.parse(open(path).read(), path)
+    found = []
+
+    def visit(node, fn):
+        for child in ast.iter_child_nodes(node):
+            name = child.name if isinstance(child, (ast.FunctionDef, ast.AsyncFunctionDef)) and fn is None else fn
+            if isinstance(child, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in child.names):
+                found.append((name, child.lineno))
+            elif isinstance(child, ast.ImportFrom) and child.module and child.module.split(".")[0] == "oracle":
+                found.append((name, child.lineno))
+            visit(child, name)
+
+    visit(tree, None)
+    return found
+
+
+def test_bench_touches_the_oracle_only_in_its_cpu_leg():
+    # the CPU baseline and the reference arm both time the oracle through cpu_oracle_sample
+    found = _oracle_imports_by_function(os.path.join(ROOT, "bench.py"))
+    assert found and all(fn == "cpu_oracle_sample" for fn, _ in found), found
+
+
+def test_graft_entry_runs_the_oracle_only_in_smoke():
+    # build() compiles the oracle's C (building the checker, not using it); smoke() compares
+    found = _oracle_imports_by_function(os.path.join(ROOT, "__graft_entry__.py"))
+    assert {fn for fn, _ in found} <= {"build", "smoke"}, found
