@@ -194,6 +194,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _cpu_model(path: str = "/proc/cpuinfo") -> str:
+    """The host CPU's model name from /proc/cpuinfo (on Arm: implementer and part codes)."""
+    fields = {}
+    try:
+        with open(path) as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    import platform
+
+    parts = [platform.machine() or "unknown"]
+    if "CPU implementer" in fields and "CPU part" in fields:
+        parts.append(f"(CPU implementer {fields['CPU implementer']}, part {fields['CPU part']})")
+    return " ".join(parts)
+
+
 def _traffic_per_launch():
     """DRAM bytes per far-field launch from the committed ncu summary, if the kernel source is unchanged."""
     try:
@@ -258,7 +278,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(WORKLOAD, precision="FP64 CPU oracle (plain C, OpenMP over rows)",
                        sample=f"{rows} sampled matvec rows per step"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": _cpu_model(),
                          "sample": f"{rows} of {V.shape[0]} matvec rows x {4 * F.shape[0]} nodes per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -476,7 +496,9 @@ def run_ours(args):
                 d32, d64 = torch.cat(list(map(torch.as_tensor, d32))), torch.cat(list(map(torch.as_tensor, d64)))
                 E32, E64 = np.asarray(E32), np.asarray(E64)
             rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-            acc = {"phi_rel_l2_fp32_vs_fp64": rel(p32, p64), "dphi_rel_l2_fp32_vs_fp64": rel(d32, d64)}
+            relmax = lambda a, b: float(torch.max(torch.abs(a - b)) / torch.max(torch.abs(b)))
+            acc = {"phi_rel_l2_fp32_vs_fp64": rel(p32, p64), "dphi_rel_l2_fp32_vs_fp64": rel(d32, d64),
+                   "phi_rel_max_fp32_vs_fp64": relmax(p32, p64), "dphi_rel_max_fp32_vs_fp64": relmax(d32, d64)}
             if batched:
                 acc["E_rel_fp32_vs_fp64_max"] = float(np.max(np.abs(E32 - E64) / np.abs(E64)))
             else:
@@ -513,7 +535,7 @@ def run_ours(args):
             V, F, N, Q = mols[big]
             val, dt, pairs, cores = cpu_oracle_sample(V, F, N, Q, args.cpu_rows, cfg)
             val1, dt1, pairs1, _ = cpu_oracle_sample(V, F, N, Q, max(8, args.cpu_rows // 16), cfg, seed=1, threads=1)
-            cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": _cpu_model(),
                    "sample": f"{min(args.cpu_rows, V.shape[0])} of {V.shape[0]} matvec rows x {4 * F.shape[0]} "
                              f"nodes ({pairs:.3g} pairs, {dt:.1f} s)" + (f", molecule {big}" if batched else ""),
                    "value_1_thread": val1,
