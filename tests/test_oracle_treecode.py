@@ -75,3 +75,35 @@ def test_treecode_error_falls_with_degree(small_problem):
         errs.append(max(np.linalg.norm(t1 - d1) / np.linalg.norm(d1), np.linalg.norm(t2 - d2) / np.linalg.norm(d2)))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 1e-4 and errs[0] / errs[2] > 10
+
+
+def test_direct_far_is_the_regular_rule_kernel_sum():
+    """The module's pair formula and node densities against the oracle's kernels K1-K4 (pinned
+    to finite differences of G0 and G_kappa) summed node by node with the regular-rule weights
+    W_{j,m,n}; and the oracle's matvec rows rebuilt from that sum, the diagonal and the 16-point
+    rule on the incident faces (Eqs. eqdbef3-eqdbef6)."""
+    V, F, N = synth.icosphere(1, 2.0)
+    orc = oracle.Problem(V, F, N, synth.ball_charges(2, 1.2, 5), 1.0, 80.0, 0.3)
+    u = np.random.default_rng(4).normal(size=2 * orc.nv)
+    nv, eps = orc.nv, orc.eps
+    y, nu, W = orc.nodes()
+    nx = tc.target_normals(orc)
+    d1, d2 = tc.direct_far(orc, u)
+    Au = orc.matvec(u)
+    for i in range(nv):
+        K = np.array([[oracle.kernels(V[i], nx[i], y[j, m], nu[j, m], eps, orc.kappa) for m in range(4)]
+                      for j in range(orc.nf)])                                # [face, node, kernel]
+        R = np.einsum("jmn,jmq->jnq", W, K)                                   # regular-rule coefficients
+        un, uu = u[nv + F], u[F]                                              # [face, corner]
+        r1 = np.sum(R[:, :, 0] * un + R[:, :, 1] * uu)
+        r2 = np.sum(R[:, :, 2] * un + R[:, :, 3] * uu)
+        assert abs(d1[i] - r1) <= 1e-12 * max(1.0, abs(r1))
+        assert abs(d2[i] - r2) <= 1e-12 * max(1.0, abs(r2))
+        # incident faces: the 16-point rule replaces the regular rule
+        c1 = c2 = 0.0
+        for j in np.flatnonzero((F == i).any(axis=1)):
+            S = orc.singular_coeffs(i, j) - R[j]
+            c1 += np.sum(S[:, 0] * un[j] + S[:, 1] * uu[j])
+            c2 += np.sum(S[:, 2] * un[j] + S[:, 3] * uu[j])
+        assert abs(Au[i] - (0.5 * (1 + eps) * u[i] - r1 - c1)) <= 1e-10 * np.abs(Au[:nv]).max()
+        assert abs(Au[nv + i] - (0.5 * (1 + 1 / eps) * u[nv + i] - r2 - c2)) <= 1e-10 * np.abs(Au[nv:]).max()
