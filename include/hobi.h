@@ -106,7 +106,9 @@ typedef struct {
   int32_t converged;     /* 1 if ||b - A u|| / ||b|| <= tol (Givens estimate) */
   double rel_residual;   /* final relative residual estimate */
   double solve_ms;       /* wall time of hobi_solve on the handle's stream (CUDA events) */
-  double farfield_pairs; /* target-source pair evaluations in the far-field kernel */
+  double farfield_pairs; /* target-source pair evaluations of the far field in the Krylov
+                            iterations (iterations x pairs per matvec; the residual matvecs
+                            of a warm start or restart are not counted) */
   double* resid_history; /* optional host buffer (caller-owned) for the residual after each it. */
   int32_t resid_capacity;/* length of resid_history (entries written: min(capacity, iterations+1)) */
 } hobi_solve_info;
