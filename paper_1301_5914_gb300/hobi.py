@@ -138,6 +138,34 @@ def _is_cuda_tensor(x) -> bool:
     return _is_torch(x) and x.is_cuda
 
 
+_PRECISIONS = {"fp32": HOBI_FP32_BULK, "fp64": HOBI_FP64}
+_SCHEMES = {"hobi": HOBI_SCHEME_HOBI, "lobi": HOBI_SCHEME_LOBI}
+
+
+def _precision(precision: str) -> int:
+    if precision not in _PRECISIONS:
+        raise ValueError(f"precision must be 'fp32' or 'fp64', not {precision!r}")
+    return _PRECISIONS[precision]
+
+
+def _scheme(scheme: str) -> int:
+    if scheme not in _SCHEMES:
+        raise ValueError(f"scheme must be 'hobi' or 'lobi', not {scheme!r}")
+    return _SCHEMES[scheme]
+
+
+def _check_mesh(V, F, N, Q=None):
+    """Shapes the C ABI reads through its plain pointers: V, N [n_v, 3], F [n_f, 3], Q [n_c, 4]."""
+    if len(V.shape) != 2 or V.shape[1] != 3:
+        raise ValueError(f"vertices must have shape (n_v, 3), not {tuple(V.shape)}")
+    if tuple(N.shape) != tuple(V.shape):
+        raise ValueError(f"vertex normals must have the shape of the vertices {tuple(V.shape)}, not {tuple(N.shape)}")
+    if len(F.shape) != 2 or F.shape[1] != 3:
+        raise ValueError(f"faces must have shape (n_f, 3), not {tuple(F.shape)}")
+    if Q is not None and (len(Q.shape) != 2 or Q.shape[1] != 4):
+        raise ValueError(f"charges must have shape (n_c, 4), not {tuple(Q.shape)}")
+
+
 def fast_plan_stats(nodes, targets, degree: int, theta: float):
     """Treecode plan statistics for FP64 source nodes and targets, built on the host (no GPU)."""
     lib = load_library()
@@ -169,10 +197,10 @@ class Solver:
         self.device_mode = _is_cuda_tensor(V)
         opt = Options()
         lib.hobi_default_options(C.byref(opt))
-        opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
+        opt.precision = _precision(precision)
         opt.restart = int(restart)
         opt.use_graph = 1 if use_graph else 0
-        opt.scheme = HOBI_SCHEME_LOBI if scheme == "lobi" else HOBI_SCHEME_HOBI
+        opt.scheme = _scheme(scheme)
         opt.autotune = 1 if autotune else 0
         opt.ff_shape = int(ff_shape)
         opt.fast_degree = int(fast_degree)
@@ -187,15 +215,24 @@ class Solver:
             opt.stream = C.c_void_p(s.cuda_stream)
             self._keep = [t.contiguous() for t in (V, F, N, charges)]
             Vt, Ft, Nt, Qt = self._keep
-            assert Vt.dtype == torch.float64 and Nt.dtype == torch.float64 and Qt.dtype == torch.float64
-            assert Ft.dtype == torch.int32
+            if not (Vt.dtype == Nt.dtype == Qt.dtype == torch.float64 and Ft.dtype == torch.int32):
+                raise TypeError("device inputs must be float64 (V, N, charges) and int32 (F) CUDA tensors")
+            if not all(_is_cuda_tensor(t) and t.device == Vt.device for t in (Ft, Nt, Qt) if t.numel()):
+                raise ValueError("device inputs must all be CUDA tensors on one device")
+            _check_mesh(Vt, Ft, Nt, Qt.reshape(-1, 4))
             ptrs = [Vt.data_ptr(), Ft.data_ptr(), Nt.data_ptr(), Qt.data_ptr() if Qt.numel() else None]
             nv, nf, nc = Vt.shape[0], Ft.shape[0], Qt.reshape(-1, 4).shape[0]
         else:
             opt.device = -1 if device is None else int(device)
             opt.mem_device = 0
             if _is_torch(V):  # host torch tensors (e.g. pinned buffers): pass their host pointers
+                import torch
+
                 self._keep = [t.contiguous() for t in (V, F, N, charges)]
+                Vt, Ft, Nt, Qt = self._keep
+                if not (Vt.dtype == Nt.dtype == Qt.dtype == torch.float64 and Ft.dtype == torch.int32):
+                    raise TypeError("host tensor inputs must be float64 (V, N, charges) and int32 (F)")
+                _check_mesh(Vt, Ft, Nt, Qt.reshape(-1, 4))
                 ptrs = [t.data_ptr() if t.numel() else None for t in self._keep]
                 nv, nf, nc = self._keep[0].shape[0], self._keep[1].shape[0], self._keep[3].reshape(-1, 4).shape[0]
             else:
@@ -203,6 +240,7 @@ class Solver:
                               np.ascontiguousarray(N, dtype=np.float64),
                               np.ascontiguousarray(charges, dtype=np.float64).reshape(-1, 4)]
                 Va, Fa, Na, Qa = self._keep
+                _check_mesh(Va, Fa, Na, Qa)
                 ptrs = [Va.ctypes.data, Fa.ctypes.data, Na.ctypes.data, Qa.ctypes.data if Qa.size else None]
                 nv, nf, nc = Va.shape[0], Fa.shape[0], Qa.shape[0]
         h = C.c_void_p()
@@ -235,10 +273,12 @@ class Solver:
 
             t = a if _is_torch(a) else torch.as_tensor(np.asarray(a))
             t = t.to(device=self._keep[0].device, dtype=torch.float64).contiguous().reshape(-1)
-            assert t.numel() == n
+            if t.numel() != n:
+                raise ValueError(f"expected {n} values, got {t.numel()}")
             return t
         a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
-        assert a.size == n
+        if a.size != n:
+            raise ValueError(f"expected {n} values, got {a.size}")
         return a
 
     def close(self):
@@ -254,7 +294,7 @@ class Solver:
 
     # ------------------------------------------------------------ API
     def set_precision(self, precision: str):
-        _check(self._lib.hobi_set_precision(self._h, HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64))
+        _check(self._lib.hobi_set_precision(self._h, _precision(precision)))
 
     def matvec(self, u):
         u = self._in(u, 2 * self.npts)
@@ -402,6 +442,10 @@ class BatchSolver:
                  device_arrays=None, fast_degree: int = 0, fast_theta: float = 0.7):
         lib = load_library()
         self._lib = lib
+        if len(molecules) == 0:
+            raise ValueError("a batch needs at least one molecule")
+        for m in molecules:
+            _check_mesh(np.asarray(m[0]), np.asarray(m[1]), np.asarray(m[2]), np.asarray(m[3]).reshape(-1, 4))
         V = np.ascontiguousarray(np.concatenate([m[0] for m in molecules]), dtype=np.float64)
         F = np.ascontiguousarray(np.concatenate([m[1] for m in molecules]), dtype=np.int32)
         N = np.ascontiguousarray(np.concatenate([m[2] for m in molecules]), dtype=np.float64)
@@ -416,7 +460,7 @@ class BatchSolver:
         self.device_mode = device_mode or device_arrays is not None
         opt = Options()
         lib.hobi_default_options(C.byref(opt))
-        opt.precision = HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64
+        opt.precision = _precision(precision)
         opt.restart = int(restart)
         opt.use_graph = 1 if use_graph else 0
         opt.fast_degree = int(fast_degree)
@@ -431,6 +475,9 @@ class BatchSolver:
             opt.stream = C.c_void_p(s.cuda_stream)
             if device_arrays is not None:  # the concatenated inputs, already resident on the GPU
                 self._keep = [t.contiguous() for t in device_arrays]
+                for t, a in zip(self._keep, (V, F, N, Q)):
+                    if tuple(t.shape) != a.shape or t.element_size() != a.itemsize:
+                        raise ValueError("device_arrays must be the concatenated V, F, N, charges of the batch")
             else:
                 self._keep = [torch.as_tensor(a, device=dev) for a in (V, F, N, Q)]
             ptrs = [t.data_ptr() for t in self._keep]
@@ -466,7 +513,7 @@ class BatchSolver:
             pass
 
     def set_precision(self, precision: str):
-        _check(self._lib.hobi_batch_set_precision(self._h, HOBI_FP32_BULK if precision == "fp32" else HOBI_FP64))
+        _check(self._lib.hobi_batch_set_precision(self._h, _precision(precision)))
 
     def split(self, a):
         """Split a concatenated per-vertex array into per-molecule arrays."""
