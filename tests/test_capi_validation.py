@@ -90,3 +90,40 @@ def test_fast_plan_stats_validation_and_counts():
     # theta -> 0: no cluster is admissible and the plan is the direct sum
     st0 = hobi.fast_plan_stats(y, V, 4, 1e-3)
     assert st0["approx_pairs"] == 0 and st0["direct_pairs"] == V.shape[0] * y.shape[0]
+
+
+def _setup_batch(lib, mesh, n_mol=2, voff=None, foff=None, qoff=None, charges=True, eps1=1.0, eps2=80.0,
+                 kappa=0.1, **opts):
+    V, F, N, Q = mesh
+    Vb, Fb, Nb, Qb = (np.ascontiguousarray(np.concatenate([a, a])) for a in (V, F, N, Q))
+    voff = np.array([0, V.shape[0], 2 * V.shape[0]] if voff is None else voff, dtype=np.int64)
+    foff = np.array([0, F.shape[0], 2 * F.shape[0]] if foff is None else foff, dtype=np.int64)
+    qoff = np.array([0, Q.shape[0], 2 * Q.shape[0]] if qoff is None else qoff, dtype=np.int64)
+    o = hobi.Options()
+    lib.hobi_default_options(C.byref(o))
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    rc = lib.hobi_setup_batch(n_mol, Vb.ctypes.data, voff.ctypes.data, Fb.ctypes.data, foff.ctypes.data,
+                              Nb.ctypes.data, Qb.ctypes.data if charges else None, qoff.ctypes.data, eps1, eps2, kappa,
+                              C.byref(o), C.byref(h))
+    return rc, lib.hobi_last_error().decode(), h.value
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(n_mol=0), "n_mol"),
+    (dict(voff=[0, 50, 42]), "non-decreasing"),
+    (dict(foff=[1, 80, 160]), "start at 0"),
+    (dict(charges=False), "charges is NULL"),
+    (dict(eps1=-1.0), "eps1, eps2 > 0"),
+    (dict(kappa=math.nan), "kappa >= 0"),
+    (dict(precision=3), "unknown precision"),
+    (dict(scheme=hobi.HOBI_SCHEME_LOBI), "HOBI scheme only"),
+    (dict(fast_degree=12), "fast_degree"),
+    (dict(fast_degree=5, fast_theta=2.0), "fast_theta"),
+    (dict(restart=500), "restart"),
+])
+def test_setup_batch_rejects_invalid_input(lib, mesh, kw, msg):
+    rc, err, h = _setup_batch(lib, mesh, **kw)
+    assert rc == hobi.HOBI_ERR_ARG and h is None
+    assert msg in err, err
