@@ -390,3 +390,19 @@ def test_regular_rule_vs_brute_force_far_face():
                 K = oracle.kernels(x, nx, xx, nn, 80.0, 0.1257)
                 sb += w * J * np.outer([1 - r - s, r, s], K)
         assert np.max(np.abs(s4 - sb)) < 1e-3 * np.max(np.abs(sb))
+
+
+def test_reaction_potential_at_interior_points_vs_kirkwood():
+    """The reaction potential at arbitrary interior points (the off-surface output) converges to
+    the Kirkwood series' reaction field (Gaussian units, 4 pi times the formulation's units):
+    measured 1.05e-3 -> 2.6e-4 relative from level 2 to 3."""
+    Q = synth.point_charge(0.5, 0, 0, 1.0)
+    pts = np.array([[0, 0, 0], [0.8, 0.3, -0.2], [-1.0, 0.5, 0.4], [0.2, -1.2, 0.6]])
+    ex = kw.reaction_potential_at(pts, Q, 2.0, 1.0, 80.0, 0.1257) / (4 * np.pi)
+    errs = []
+    for L in (2, 3):
+        V, F, N = synth.icosphere(L, 2.0)
+        p = oracle.Problem(V, F, N, Q, 1.0, 80.0, 0.1257)
+        u = p.gmres(1e-10)[0]
+        errs.append(np.abs(p.reaction_potential(u, pts) - ex).max() / np.abs(ex).max())
+    assert errs[1] < errs[0] / 3 and errs[1] < 5e-4
