@@ -49,3 +49,28 @@ def test_synthetic_molecule_surface():
     # every charge (atom centre) is inside: nearest surface vertex is farther than 0.5 A
     d = np.min(np.linalg.norm(V[None, :, :] - Q[:, None, :3], axis=2), axis=1)
     assert np.all(d > 0.5)
+
+
+def test_two_globule_complex_is_one_closed_surface():
+    """The C5 recipe at a small size: two seeded globules in contact give one closed, oriented
+    surface (Euler characteristic 2), both globules' charges inside it, reproducible."""
+    V, F, N, Q = synth.two_globule_complex(60, 51, 52, n_faces=6000)
+    st = synth.mesh_stats(V, F)
+    assert st["closed_oriented"] and st["euler"] == 2
+    assert Q.shape[0] == 120 and abs(F.shape[0] - 6000) < 0.15 * 6000
+    assert np.allclose(np.linalg.norm(N, axis=1), 1.0)
+    # the two halves: atoms of each globule on either side of the contact plane
+    rg = 20.0 * (60 / 1000.0) ** (1.0 / 3.0)
+    assert np.median(Q[:60, 0]) < rg - 1.0 < np.median(Q[60:, 0])
+    d = np.min(np.linalg.norm(V[None, :, :] - Q[:, None, :3], axis=2), axis=1)
+    assert np.all(d > 0.5)
+    V2, F2, N2, Q2 = synth.two_globule_complex(60, 51, 52, n_faces=6000)
+    assert np.array_equal(V, V2) and np.array_equal(F, F2)
+
+
+def test_point_charge_and_icosphere_radius():
+    q = synth.point_charge(0.5, -0.25, 0.0, 2.0)
+    assert q.shape == (1, 4) and np.array_equal(q[0], [0.5, -0.25, 0.0, 2.0])
+    V, F, N = synth.icosphere(3, 2.5, center=(1.0, 0.0, -1.0))
+    r = np.linalg.norm(V - [1.0, 0.0, -1.0], axis=1)
+    assert np.allclose(r, 2.5) and np.allclose(N, (V - [1.0, 0.0, -1.0]) / 2.5)
