@@ -33,8 +33,10 @@ rules of this implementation:
   formula above with the proxies as sources.
 
 The paper prints no fast summation to compare with. The tests pin this module to the direct sum
-(a tiny theta gives it to rounding, the error falls with the degree) and to polynomial
-reproduction and partition of unity of the interpolation.
+(a tiny theta gives it to rounding, the error falls with the degree), to polynomial reproduction
+and partition of unity of the interpolation, and its pair formula and node densities to the
+oracle's kernels K1-K4 (themselves pinned to finite differences of G0 and G_kappa) summed with the
+regular-rule weights.
 """
 from __future__ import annotations
 
