@@ -57,3 +57,30 @@ def test_option_strings_and_dtypes(mesh):
     with pytest.raises(TypeError):
         hobi.Solver(*(torch.as_tensor(a, dtype=torch.float32) if a.dtype.kind == "f" else torch.as_tensor(a)
                       for a in (V, F.astype(np.int32), N, Q)), 1.0, 80.0, 0.1)
+
+
+class _FakeStream:
+    cuda_stream = 0
+
+
+def test_device_mode_branches_run_up_to_the_library(mesh, monkeypatch):
+    """The device-pointer branches of Solver and BatchSolver, exercised on the host by treating
+    CPU tensors as device tensors: every check runs, wrong inputs are refused, and valid ones
+    reach the library (which, without a GPU, reports a CUDA error)."""
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the real device path is covered by the GPU tests")
+    V, F, N, Q = mesh
+    monkeypatch.setattr(hobi, "_is_cuda_tensor", lambda x: hobi._is_torch(x))
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    t = [torch.as_tensor(a) for a in (V, F.astype(np.int32), N, Q)]
+    _reaches_library(lambda: hobi.Solver(*t, 1.0, 80.0, 0.1, device=0, stream=_FakeStream()))
+    with pytest.raises(TypeError):
+        hobi.Solver(t[0], t[1].long(), t[2], t[3], 1.0, 80.0, 0.1, device=0, stream=_FakeStream())
+    with pytest.raises(ValueError):
+        hobi.Solver(t[0], t[1], t[2][:-1], t[3], 1.0, 80.0, 0.1, device=0, stream=_FakeStream())
+    mols = [(V, F, N, Q), (V, F, N, Q)]
+    cat = [torch.as_tensor(np.concatenate([m[k] for m in mols])) for k in range(4)]
+    cat[1] = cat[1].to(torch.int32)
+    _reaches_library(lambda: hobi.BatchSolver(mols, 1.0, 80.0, 0.1, device_arrays=cat, stream=_FakeStream()))
+    with pytest.raises(ValueError):
+        hobi.BatchSolver(mols, 1.0, 80.0, 0.1, device_arrays=[cat[0][:-1], *cat[1:]], stream=_FakeStream())
