@@ -258,6 +258,14 @@ int hobi_fast_plan_stats(const double* nodes, int64_t n_nodes, const double* tar
                          int32_t degree, double theta, int64_t* direct_pairs, int64_t* approx_pairs,
                          int32_t* batches, int32_t* proxy_clusters);
 
+/* Accuracy accessor of the FP64 far field's own pair functions, evaluated on the current CUDA
+ * device: rsqrt_x[k] = 1/sqrt(x[k]) (MUFU seed + one Newton step) and exp_neg_x[k] = exp(-x[k])
+ * (64-entry table of 2^(j/64) + degree-5 polynomial), exactly as the FP64 kernels compute
+ * 1/r and e^{-kappa r} (kernels of Eq. (10) in the paper). x: n host doubles, finite and >= 0
+ * (x = 0 gives rsqrt inf); n <= 2^24. All three arrays are HOST arrays. Allocates and frees
+ * temporary device memory. */
+int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x);
+
 /* Free every resource of the handle (NULL is a no-op). */
 void hobi_destroy(hobi_t h);
 

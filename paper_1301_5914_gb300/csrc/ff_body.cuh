@@ -233,13 +233,85 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
                                                        out, sh, bars, phases, err);
 }
 
-// One block's share of the FP64 far field (2 targets per thread); sh: 4 kTile double2.
-template <bool ROW2, bool SKIP_SELF = false>
+// ---- FP64 pair primitives. GB300 runs double-precision FMA/add/multiply at about 1/64 of the
+// FP32 rate, but its MUFU pipe returns 1/sqrt and 1/x seeds for doubles (rsqrt.approx.f64) at the
+// FP32 MUFU rate, and integer work runs beside both. So the FP64 far field takes 1/r from the MUFU
+// seed plus one Newton step, and exp(-kappa r) from a table plus a short polynomial, instead of the
+// library's full-range sqrt, division and exp: 45 FP64-pipe operations per pair instead of ~70.
+
+// 1/sqrt(x), x > 0 normal: seed y0 = rsqrt.approx.f64(x), then with e = 1 - x y0^2 (so that
+// x y0^2 = 1 - e), 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)). With the seed's
+// relative error below 2^-20 the truncation is below 2^-58; the result is within a few units in
+// the last place (checked against numpy in the tests). 5 FP64 operations (+1 MUFU).
+__device__ __forceinline__ double rsqrt_f64(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double t = x * y;
+  const double e = fma(-t, y, 1.0);
+  const double p = fma(e, 0.375, 0.5);
+  return fma(y * e, p, y);
+}
+
+// 2^(j/64), j = 0..63, in shared memory: each far-field block fills it once (exp2 from the CUDA
+// math library; 64 evaluations per block).
+constexpr int kExpTable = 64;
+__device__ __forceinline__ void exp_table_init(double* tab) {
+  for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) tab[j] = exp2((double)j / kExpTable);
+}
+
+// 2^(t/64) for t <= 0 by Tang's table-driven method (ACM TOMS 15(2), 1989) with a 64-entry table:
+// t = n + f with n = round(t) (the 1.5 * 2^52 shift puts n in the low word) and |f| <= 1/2 exact,
+// 2^(t/64) = 2^floor(n/64) * 2^((n mod 64)/64) * exp(f ln2/64), the last factor by its Taylor
+// polynomial of degree 5 (|f ln2/64| <= 0.0055, truncation below 4e-17). The power of two is
+// added to the exponent field; n is clamped at -64 * 1021 (the result stays a normal double, at
+// most 2^-1020), so t below that (e^-707.7 and smaller: padding nodes, distant pairs) gives a
+// value within 5e-308 of the true one.
+// 3 + 5 + 1 FP64 operations; the rest is integer work.
+__device__ __forceinline__ double exp2_64th(double t, const double* __restrict__ tab) {
+  constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
+  constexpr double c = 0.693147180559945309417232121458 / 64.0;  // ln(2) / 64
+  constexpr double k2 = c * c / 2.0, k3 = k2 * c / 3.0, k4 = k3 * c / 4.0, k5 = k4 * c / 5.0;
+  const double nd = t + kShift;
+  const double f = t - (nd - kShift);
+  const int n = max(__double2loint(nd), -64 * 1021);
+  const double p = fma(fma(fma(fma(fma(k5, f, k4), f, k3), f, k2), f, c), f, 1.0);
+  const double v = tab[n & (kExpTable - 1)] * p;
+  return __hiloint2double(__double2hiint(v) + (n >> 6) * (1 << 20), __double2loint(v));
+}
+
+// Per-launch constants of the FP64 pair arithmetic (row 1 is summed divided by eps).
+struct FF64Consts {
+  double c64;         // -64 log2(e) (kappa-scaled tables) or -64 kappa log2(e): 2^(c64 r / 64) = E
+  double kap, kap_sq; // unscaled mode: kappa, kappa^2
+  double omie;        // 1 - 1/eps
+  double row1_scale;  // eps xs
+  double row2_scale;  // xs^2
+};
+inline FF64Consts ff64_consts(double eps, double kappa) {
+  const double xs = ff32_coord_scale(kappa);
+  constexpr double kLog2e = 1.44269504088896340735992468100;
+  FF64Consts c;
+  c.c64 = -64.0 * kLog2e * (ff32_kappa_scaled(kappa) ? 1.0 : kappa);
+  c.kap = kappa;
+  c.kap_sq = kappa * kappa;
+  c.omie = 1.0 - 1.0 / eps;
+  c.row1_scale = eps * xs;
+  c.row2_scale = xs * xs;
+  return c;
+}
+
+// One block's share of the FP64 far field (2 targets per thread): targets bx*NT*T ... of nt,
+// source tiles [t0, t1) of kTile nodes; sh: 4 kTile double2, tab: the exp table (initialised,
+// with a __syncthreads() between, before the first call). The FP32 kernel's multiplied-out pair
+// formula in double precision, with the same table layout:
+//   targets: {xs (x - c), 0, nu_x, 0}; sources: {-xs (y - c), sigma/eps, xs m, sigma/eps - sigma}
+// where xs = kappa for kappa-scaled tables (KS), else 1; then kappa r is the scaled r (KS).
+template <bool ROW2, bool KS, bool SKIP_SELF = false>
 __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int nt, const double* __restrict__ src,
-                                           int t0, int t1, double kap, double eps, double ieps,
-                                           double* __restrict__ out, int bx, double2* sh) {
+                                           int t0, int t1, const FF64Consts& cs, double* __restrict__ out, int bx,
+                                           double2* sh, const double* __restrict__ tab) {
   constexpr int T = kFF64Targets, NT = kFF64Threads;
-  double px[T], py[T], pz[T], qx[T], qy[T], qz[T], a1[T], a2[T];
+  double px[T], py[T], pz[T], qx[T], qy[T], qz[T], a1[T], wx[T], wy[T], wz[T];
   const int base = bx * (NT * T) + threadIdx.x;
 #pragma unroll
   for (int k = 0; k < T; ++k) {
@@ -247,7 +319,7 @@ __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int n
     const double* t = tgt + 8 * (size_t)i;
     px[k] = t[0]; py[k] = t[1]; pz[k] = t[2];
     qx[k] = t[4]; qy[k] = t[5]; qz[k] = t[6];
-    a1[k] = a2[k] = 0.0;
+    a1[k] = wx[k] = wy[k] = wz[k] = 0.0;
   }
   for (int tile = t0; tile < t1; ++tile) {
     __syncthreads();
@@ -255,25 +327,29 @@ __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int n
     for (int q = threadIdx.x; q < 4 * kTile; q += NT) sh[q] = g[q];
     __syncthreads();
     for (int s = 0; s < kTile; ++s) {
-      const double2 y01 = sh[4 * s], y2s = sh[4 * s + 1], m01 = sh[4 * s + 2], m2 = sh[4 * s + 3];
+      const double2 A = sh[4 * s], B = sh[4 * s + 1], C = sh[4 * s + 2], D = sh[4 * s + 3];
 #pragma unroll
       for (int k = 0; k < T; ++k) {
-        double dx = px[k] - y01.x, dy = py[k] - y01.y, dz = pz[k] - y2s.x;
-        double r2 = dx * dx + dy * dy + dz * dz;
-        double r = sqrt(r2);
-        double ir = (SKIP_SELF && !(r2 > 0.0)) ? 0.0 : 1.0 / r;
-        double kr = kap * r;
-        double E = exp(-kr);
-        double P = E * (1.0 + kr);
-        double aym = dx * m01.x + dy * m01.y + dz * m2.x;
-        double ir3 = ir * ir * ir;
-        a1[k] += (1.0 - E) * ir * y2s.y + (eps * P - 1.0) * ir3 * aym;
+        const double dx = px[k] + A.x, dy = py[k] + A.y, dz = pz[k] + B.x;
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        double ir = rsqrt_f64(r2);
+        if (SKIP_SELF) ir = r2 > 0.0 ? ir : 0.0;  // every term of a zero-distance pair then vanishes
+        const double r = r2 * ir;
+        const double E = exp2_64th(r * cs.c64, tab);
+        const double Pm1 = fma(E, KS ? r + 1.0 : fma(cs.kap, r, 1.0), -1.0);  // P - 1
+        const double aym = fma(dz, D.x, fma(dy, C.y, dx * C.x));             // d . m
+        const double ir2 = ir * ir;
+        const double v = aym * ir2;
+        // row 1 / eps = [ (1 - E) sigma/eps + (P - 1 + 1 - 1/eps) v ] / r
+        a1[k] = fma(fma(Pm1 + cs.omie, v, fma(-E, B.y, B.y)), ir, a1[k]);
         if (ROW2) {
-          double Q3 = E * (3.0 + kr * (3.0 + kr)) - 3.0;
-          double ir5 = ir3 * ir * ir;
-          double w = (P - 1.0) * ir3;
-          double sv = (P * ieps - 1.0) * ir3 * y2s.y - Q3 * ir5 * aym;
-          a2[k] += qx[k] * (w * m01.x + sv * dx) + qy[k] * (w * m01.y + sv * dy) + qz[k] * (w * m2.x + sv * dz);
+          // S = (P - 1)(sigma/eps - 3 v) + (sigma/eps - sigma) - E kappa^2 (d . m)
+          const double S = fma(KS ? -E : -E * cs.kap_sq, aym, fma(Pm1, fma(-3.0, v, B.y), D.y));
+          const double ir3 = ir2 * ir;
+          const double w = Pm1 * ir3, sv = S * ir3;
+          wx[k] = fma(w, C.x, fma(sv, dx, wx[k]));
+          wy[k] = fma(w, C.y, fma(sv, dy, wy[k]));
+          wz[k] = fma(w, D.x, fma(sv, dz, wz[k]));
         }
       }
     }
@@ -282,8 +358,8 @@ __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int n
   for (int k = 0; k < T; ++k) {
     int i = base + k * NT;
     if (i < nt) {
-      out[i] = a1[k];
-      if (ROW2) out[nt + i] = a2[k];
+      out[i] = a1[k] * cs.row1_scale;
+      if (ROW2) out[nt + i] = fma(qx[k], wx[k], fma(qy[k], wy[k], qz[k] * wz[k])) * cs.row2_scale;
     }
   }
 }
@@ -316,10 +392,13 @@ __device__ __forceinline__ void gather32_node(int node, int nv, const int* __res
   o[3] = make_float4(mz, mz, sd, sd);
 }
 
+// FP64 layout of the same node: {-xs y}, sigma/eps, {m = xs mu nu_y}, sigma/eps - sigma (y
+// relative to the centroid c), one double each.
 __device__ __forceinline__ void gather64_node(int node, int nv, const int* __restrict__ F,
                                               const double* __restrict__ ny, const double* __restrict__ nnu,
                                               const double* __restrict__ nW, const double* __restrict__ center,
-                                              const double* __restrict__ u, double* __restrict__ src) {
+                                              const double* __restrict__ u, double inv_eps, double xs,
+                                              double* __restrict__ src) {
   int j = node >> 2;
   int a = F[3 * j], b = F[3 * j + 1], c = F[3 * j + 2];
   const double* W = nW + 3 * (size_t)node;
@@ -327,15 +406,16 @@ __device__ __forceinline__ void gather64_node(int node, int nv, const int* __res
   double mu = (W[0] * u[a] + W[1] * u[b] + W[2] * u[c]) * kInv4Pi;
   const double* y = ny + 3 * (size_t)node;
   const double* n = nnu + 3 * (size_t)node;
+  const double xm = xs * mu;
   double* o = src + 8 * (size_t)node;
-  o[0] = y[0] - center[0];
-  o[1] = y[1] - center[1];
-  o[2] = y[2] - center[2];
-  o[3] = sig;
-  o[4] = mu * n[0];
-  o[5] = mu * n[1];
-  o[6] = mu * n[2];
-  o[7] = 0.0;
+  o[0] = xs * (center[0] - y[0]);
+  o[1] = xs * (center[1] - y[1]);
+  o[2] = xs * (center[2] - y[2]);
+  o[3] = sig * inv_eps;
+  o[4] = xm * n[0];
+  o[5] = xm * n[1];
+  o[6] = xm * n[2];
+  o[7] = sig * inv_eps - sig;
 }
 
 // LOBI-PB node = face j: centroid y_j, face normal nu_j, weight A_j (area), densities from the
@@ -363,20 +443,21 @@ __device__ __forceinline__ void gather32_lobi(int j, int nf, const double* __res
 __device__ __forceinline__ void gather64_lobi(int j, int nf, const double* __restrict__ ny,
                                               const double* __restrict__ nnu, const double* __restrict__ nW,
                                               const double* __restrict__ center, const double* __restrict__ u,
-                                              double* __restrict__ src) {
+                                              double inv_eps, double xs, double* __restrict__ src) {
   const double A = nW[3 * (size_t)j];
   const double sig = A * u[nf + j] * kInv4Pi, mu = A * u[j] * kInv4Pi;
   const double* y = ny + 3 * (size_t)j;
   const double* n = nnu + 3 * (size_t)j;
+  const double xm = xs * mu;
   double* o = src + 8 * (size_t)j;
-  o[0] = y[0] - center[0];
-  o[1] = y[1] - center[1];
-  o[2] = y[2] - center[2];
-  o[3] = sig;
-  o[4] = mu * n[0];
-  o[5] = mu * n[1];
-  o[6] = mu * n[2];
-  o[7] = 0.0;
+  o[0] = xs * (center[0] - y[0]);
+  o[1] = xs * (center[1] - y[1]);
+  o[2] = xs * (center[2] - y[2]);
+  o[3] = sig * inv_eps;
+  o[4] = xm * n[0];
+  o[5] = xm * n[1];
+  o[6] = xm * n[2];
+  o[7] = sig * inv_eps - sig;
 }
 
 // Au_i = (1/2)(1+eps) u_i - [sum_c part_c,i + sum over incident entries of corr . (u_{N_v+v}, u_v)]

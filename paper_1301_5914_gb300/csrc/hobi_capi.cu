@@ -78,7 +78,7 @@ struct hobi_ctx {
   int* zero_ptr = nullptr;  // LOBI: an all-zero incidence row pointer (no singular correction)
   int* ff_err = nullptr;    // far-field tile pipeline timeout flag (device)
   double eps1 = 1, eps2 = 80, kappa = 0, eps = 80;
-  double xs = 1;            // coordinate scale of the FP32 tables (ff32_coord_scale(kappa))
+  double xs = 1;            // coordinate scale of the far-field tables (ff32_coord_scale(kappa))
   int num_sms = 1;
   // fast summation (treecode) of the FP32 far field; fast_degree 0: direct summation
   int fast_degree = 0, fast_chunks = 1, fast_ntasks = 0, fast_nup = 0, fast_npc = 0, fast_resident = 1;
@@ -1240,6 +1240,24 @@ int hobi_fast_plan_stats(const double* nodes, int64_t n_nodes, const double* tar
   if (approx_pairs) *approx_pairs = P.approx_pairs;
   if (batches) *batches = (int32_t)P.batch.size();
   if (proxy_clusters) *proxy_clusters = (int32_t)P.pc_offset.size();
+  return HOBI_OK;
+}
+
+int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x) {
+  if (n < 0 || n > (int64_t)1 << 24) return fail(HOBI_ERR_ARG, "n must be in [0, 2^24]");
+  if (n == 0) return HOBI_OK;
+  if (!x || !rsqrt_x || !exp_neg_x) return fail(HOBI_ERR_ARG, "NULL argument");
+  for (int64_t k = 0; k < n; ++k)
+    if (!(x[k] >= 0.0 && x[k] < 1e300)) return fail(HOBI_ERR_ARG, "x must be finite and non-negative");
+  double* d = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  if (cudaMalloc(&d, 3 * bytes) != cudaSuccess) return fail(HOBI_ERR_NOMEM, "cudaMalloc failed");
+  cudaError_t e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_fp64_pair_functions(d, n, d + n, d + 2 * n, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(rsqrt_x, d + n, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(exp_neg_x, d + 2 * n, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(HOBI_ERR_CUDA, std::string("hobi_fp64_pair_functions: ") + cudaGetErrorString(e));
   return HOBI_OK;
 }
 

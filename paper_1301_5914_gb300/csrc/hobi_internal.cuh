@@ -8,12 +8,14 @@
 //   inc_ptr[n_v+1], inc_face[3 n_f]                            vertex -> incident faces (sorted)
 //   corr[3 n_f][3][4]         singular correction per (vertex, incident face) entry (FP64)
 //   tgt32[n_v][2] float4      target xs (x - c) and unit normal (FP32 path)
+//   tgt64[n_v][8] double      {xs (x - c), 0, unit normal, 0} (FP64 path)
 //   src32[n_pad][4] float4    per node, each value twice for paired FP32 math, rebuilt per matvec:
 //                             {-xs y}, {sigma/eps}, {m = xs mu nu_y}, {sigma/eps - sigma}
 //                             (y relative to c; sigma, mu / 4pi; xs = ff32_coord_scale(kappa))
-//   src64[n_pad][8] double    (y - c, sigma/4pi, mu nu_y/4pi, 0) per node (FP64 path)
+//   src64[n_pad][8] double    per node, rebuilt per matvec: -xs y, sigma/eps, m = xs mu nu_y,
+//                             sigma/eps - sigma (FP64 path; the FP32 quantities, once each)
 //   part[chunks][2 n_v]       FP64 far-field partial sums per source chunk
-// c is the vertex centroid: both precisions work in coordinates relative to it.
+// c is the vertex centroid: both precisions work in coordinates relative to it, scaled by xs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -100,7 +102,7 @@ inline FF32Consts ff32_consts(double eps, double kappa) {
   c.row2_scale = xs * xs;
   return c;
 }
-// xs: ff32_coord_scale(kappa), applied to the FP32 copies only.
+// xs: ff32_coord_scale(kappa), applied to the coordinates of both the FP32 and the FP64 tables.
 cudaError_t launch_targets(int nv, const double* V, const double* Nv, const double* center, double xs,
                            float4* tgt32, double* tgt64, cudaStream_t s);
 cudaError_t launch_points(int np, const double* P, int stride, const double* center, double xs, float4* tgt32,
@@ -136,6 +138,9 @@ int farfield_blocks_per_sm(bool fp32, bool row2, int shape = 0);
 cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt32, const double* tgt64,
                             const float4* src32, const double* src64, double eps, double kappa,
                             double* part, int* err, cudaStream_t s, bool skip_self = false);
+// The FP64 far field's own 1/sqrt(x) and exp(-x) on n points (device arrays).
+cudaError_t launch_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x,
+                                       cudaStream_t s);
 // LOBI-PB node densities (one node per face)
 cudaError_t launch_gather_lobi(bool fp32, int nf, const double* ny, const double* nnu, const double* nW,
                                const double* center, const double* u, const int* kptr, int64_t ld, double inv_eps,
@@ -194,7 +199,7 @@ struct MolDesc {          // one molecule's device tables (owned by its single-m
   double* part;           // [chunks][2 nv] partials of the batched far field
   int nv, n_nodes, chunks;
   double eps;
-  double xs;              // FP32 coordinate scale (ff32_coord_scale)
+  double xs;              // coordinate scale of the far-field tables (ff32_coord_scale)
   int64_t u_off;          // offset of the molecule's 2 nv block in the concatenated vectors
   // fast summation of the FP32 far field (fast = 1): tree-ordered node and proxy entries,
   // batch-ordered targets, segments, and the upward tables; fchunks partial rows

@@ -62,7 +62,7 @@ __global__ void k_gather_batch(bool fp32, const MolDesc* __restrict__ mols, int 
     ff::gather32_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.xs, d.fast ? d.fsrc : d.src32,
                       d.fast ? d.fpos[node] : node);
   else
-    ff::gather64_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, d.src64);
+    ff::gather64_node(node, d.nv, d.F, d.ny, d.nnu, d.nW, d.center, um, 1.0 / d.eps, d.xs, d.src64);
 }
 
 // Batched FP32 far field: one one-warp block per task (molecule, target block, source tiles
@@ -98,11 +98,14 @@ __global__ void __launch_bounds__(kBatchFF32Threads, 8)
 
 // Batched FP64 far field: persistent blocks pull tasks from an atomic counter (reset to 0 before
 // each launch) until the list is exhausted; tasks of converged molecules are skipped.
+template <bool KS>
 __global__ void __launch_bounds__(kFF64Threads)
     k_farfield_batch64(const MolDesc* __restrict__ mols, const FFTask* __restrict__ tasks, int ntasks, int* counter,
-                       const MolState* ms, double kap, double eps) {
+                       const MolState* ms, ff::FF64Consts cs) {
   __shared__ double2 sh[4 * kTile];
+  __shared__ double tab[ff::kExpTable];
   __shared__ int s_task;
+  ff::exp_table_init(tab);  // read only after the barriers below
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
     __syncthreads();
@@ -112,8 +115,8 @@ __global__ void __launch_bounds__(kFF64Threads)
     const FFTask tk = tasks[t];
     if (mol_done(ms, tk.mol)) continue;
     const MolDesc& d = mols[tk.mol];
-    ff::ff64_block<true>(d.tgt64, d.nv, d.src64, tk.t0, tk.t1, kap, eps, 1.0 / eps,
-                         d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx, sh);
+    ff::ff64_block<true, KS>(d.tgt64, d.nv, d.src64, tk.t0, tk.t1, cs, d.part + (size_t)tk.chunk * 2 * d.nv, tk.bx,
+                             sh, tab);
   }
 }
 
@@ -331,7 +334,10 @@ cudaError_t launch_farfield_batch(bool fp32, const MolDesc* mols, const FFTask* 
   } else {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_farfield_batch64<<<grid, kFF64Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, kappa, eps);
+    if (ff32_kappa_scaled(kappa))
+      k_farfield_batch64<true><<<grid, kFF64Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff::ff64_consts(eps, kappa));
+    else
+      k_farfield_batch64<false><<<grid, kFF64Threads, 0, s>>>(mols, tasks, ntasks, counter, ms, ff::ff64_consts(eps, kappa));
   }
   return cudaGetLastError();
 }
@@ -343,7 +349,7 @@ int farfield_batch_blocks_per_sm(bool fp32, double kappa) {
   else if (fp32)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch32<false>, kBatchFF32Threads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch64, kFF64Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield_batch64<true>, kFF64Threads, 0);
   return n > 0 ? n : 1;
 }
 

@@ -53,11 +53,11 @@ __global__ void k_gather32(int n_nodes, int nv, const int* __restrict__ F, const
 __global__ void k_gather64(int n_nodes, int nv, const int* __restrict__ F, const double* __restrict__ ny,
                            const double* __restrict__ nnu, const double* __restrict__ nW,
                            const double* __restrict__ center, const double* __restrict__ u, const int* kptr,
-                           int64_t ld, double* __restrict__ src) {
+                           int64_t ld, double inv_eps, double xs, double* __restrict__ src) {
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= n_nodes) return;
   if (kptr) u += (int64_t)(*kptr) * ld;
-  ff::gather64_node(node, nv, F, ny, nnu, nW, center, u, src);
+  ff::gather64_node(node, nv, F, ny, nnu, nW, center, u, inv_eps, xs, src);
 }
 
 __global__ void k_gather_lobi(bool fp32, int nf, const double* __restrict__ ny, const double* __restrict__ nnu,
@@ -70,7 +70,7 @@ __global__ void k_gather_lobi(bool fp32, int nf, const double* __restrict__ ny, 
   if (fp32)
     ff::gather32_lobi(j, nf, ny, nnu, nW, center, u, inv_eps, xs, src32);
   else
-    ff::gather64_lobi(j, nf, ny, nnu, nW, center, u, src64);
+    ff::gather64_lobi(j, nf, ny, nnu, nW, center, u, inv_eps, xs, src64);
 }
 
 // Padding nodes: far away with zero densities, so every term they add is exactly zero.
@@ -108,14 +108,29 @@ __global__ void __launch_bounds__(NT, ff32_min_blocks<NT, TP>())
                                                     err);
 }
 
-template <bool ROW2, bool SKIP_SELF = false>
+template <bool ROW2, bool KS, bool SKIP_SELF>
 __global__ void __launch_bounds__(kFF64Threads)
     k_farfield64(const double* __restrict__ tgt, int nt, const double* __restrict__ src, int n_tiles, int tpc,
-                 double kap, double eps, double ieps, double* __restrict__ part, int64_t ldp) {
+                 ff::FF64Consts cs, double* __restrict__ part, int64_t ldp) {
   __shared__ double2 sh[4 * kTile];
+  __shared__ double tab[ff::kExpTable];
+  ff::exp_table_init(tab);  // read only after the tile loop's first __syncthreads()
   const int t0 = blockIdx.y * tpc;
-  ff::ff64_block<ROW2, SKIP_SELF>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), kap, eps, ieps, part + (size_t)blockIdx.y * ldp,
-                       blockIdx.x, sh);
+  ff::ff64_block<ROW2, KS, SKIP_SELF>(tgt, nt, src, t0, min(n_tiles, t0 + tpc), cs, part + (size_t)blockIdx.y * ldp,
+                                      blockIdx.x, sh, tab);
+}
+
+// The FP64 far field's 1/sqrt(x) and exp(-x), element by element (accuracy tests).
+__global__ void k_fp64_pair_functions(const double* __restrict__ x, int64_t n, double* __restrict__ rs,
+                                      double* __restrict__ ex) {
+  __shared__ double tab[ff::kExpTable];
+  ff::exp_table_init(tab);
+  __syncthreads();
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  constexpr double kNegLog2e64 = -64.0 * 1.44269504088896340735992468100;
+  rs[k] = x[k] > 0.0 ? ff::rsqrt_f64(x[k]) : 1.0 / 0.0;
+  ex[k] = ff::exp2_64th(x[k] * kNegLog2e64, tab);
 }
 
 // ------------------------------------------------------------------ combine
@@ -164,7 +179,8 @@ cudaError_t launch_gather(bool fp32, int n_nodes, int nv, const int* F, const do
     k_gather32<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, xs,
                                                   src32, pos);
   else
-    k_gather64<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, src64);
+    k_gather64<<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, nv, F, ny, nnu, nW, center, u, kptr, ld, inv_eps, xs,
+                                                  src64);
   return cudaGetLastError();
 }
 
@@ -232,9 +248,9 @@ int farfield_blocks_per_sm(bool fp32, bool row2, int shape) {
   int n = 1;
   if (fp32) return row2 ? occupancy32<true, false>(shape) : occupancy32<false, false>(shape);
   if (row2)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<true>, kFF64Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<true, true, false>, kFF64Threads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<false>, kFF64Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_farfield64<false, true, false>, kFF64Threads, 0);
   return n > 0 ? n : 1;
 }
 
@@ -292,15 +308,25 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
               : launch32_shape<false, false, false>(p.shape, grid, tgt32, nt, src32, nti, tpc, cs, part, ldp, err, s);
   }
   dim3 grid((p.n_targets + kFF64Threads * kFF64Targets - 1) / (kFF64Threads * kFF64Targets), p.chunks);
-  if (p.row2 && skip_self)
-    k_farfield64<true, true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk,
-                                                           kappa, eps, 1.0 / eps, part, ldp);
-  else if (p.row2)
-    k_farfield64<true><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk, kappa,
-                                                     eps, 1.0 / eps, part, ldp);
-  else
-    k_farfield64<false><<<grid, kFF64Threads, 0, s>>>(tgt64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk, kappa,
-                                                      eps, 1.0 / eps, part, ldp);
+  const ff::FF64Consts cs = ff::ff64_consts(eps, kappa);
+  const bool ks = ff32_kappa_scaled(kappa);
+  const int nt = p.n_targets, nti = p.n_tiles, tpc = p.tiles_per_chunk;
+  if (p.row2 && skip_self) {
+    if (ks) k_farfield64<true, true, true><<<grid, kFF64Threads, 0, s>>>(tgt64, nt, src64, nti, tpc, cs, part, ldp);
+    else k_farfield64<true, false, true><<<grid, kFF64Threads, 0, s>>>(tgt64, nt, src64, nti, tpc, cs, part, ldp);
+  } else if (p.row2) {
+    if (ks) k_farfield64<true, true, false><<<grid, kFF64Threads, 0, s>>>(tgt64, nt, src64, nti, tpc, cs, part, ldp);
+    else k_farfield64<true, false, false><<<grid, kFF64Threads, 0, s>>>(tgt64, nt, src64, nti, tpc, cs, part, ldp);
+  } else {
+    if (ks) k_farfield64<false, true, false><<<grid, kFF64Threads, 0, s>>>(tgt64, nt, src64, nti, tpc, cs, part, ldp);
+    else k_farfield64<false, false, false><<<grid, kFF64Threads, 0, s>>>(tgt64, nt, src64, nti, tpc, cs, part, ldp);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x,
+                                       cudaStream_t s) {
+  if (n > 0) k_fp64_pair_functions<<<nblk(n, 256), 256, 0, s>>>(x, n, rsqrt_x, exp_neg_x);
   return cudaGetLastError();
 }
 

@@ -438,7 +438,7 @@ __global__ void k_targets(int nv, const double* V, const double* Nv, const doubl
   t32[2 * i] = make_float4((float)(xs * x.x), (float)(xs * x.y), (float)(xs * x.z), 0.f);
   t32[2 * i + 1] = make_float4((float)n.x, (float)n.y, (float)n.z, 0.f);
   double* o = t64 + 8 * (size_t)i;
-  o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = 0.0;
+  o[0] = xs * x.x; o[1] = xs * x.y; o[2] = xs * x.z; o[3] = 0.0;
   o[4] = n.x; o[5] = n.y; o[6] = n.z; o[7] = 0.0;
 }
 
@@ -450,7 +450,7 @@ __global__ void k_points(int np, const double* P, int stride, const double* cent
   t32[2 * i] = make_float4((float)(xs * x.x), (float)(xs * x.y), (float)(xs * x.z), 0.f);
   t32[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
   double* o = t64 + 8 * (size_t)i;
-  o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = 0.0;
+  o[0] = xs * x.x; o[1] = xs * x.y; o[2] = xs * x.z; o[3] = 0.0;
   o[4] = 0.0; o[5] = 0.0; o[6] = 0.0; o[7] = 0.0;
 }
 

@@ -37,7 +37,7 @@ EXPORTS = [
     "hobi_solve", "hobi_solve_from", "hobi_solve_refined", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
     "hobi_reaction_potential_noalloc", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
-    "hobi_fast_info", "hobi_fast_plan_stats",
+    "hobi_fast_info", "hobi_fast_plan_stats", "hobi_fp64_pair_functions",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
     "hobi_matvec_batch", "hobi_solve_batch", "hobi_energy_batch", "hobi_batch_kernel_launches", "hobi_destroy_batch",
     "hobi_batch_profile_enable", "hobi_batch_profile_read",
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH):
                                    C.POINTER(C.c_int32)]
     lib.hobi_fast_plan_stats.argtypes = [dp, i64, dp, i64, C.c_int32, C.c_double, C.POINTER(i64), C.POINTER(i64),
                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.hobi_fp64_pair_functions.argtypes = [dp, i64, dp, dp]
     lib.hobi_destroy.argtypes = [vp]
     lib.hobi_destroy.restype = None
     lib.hobi_setup_batch.argtypes = [C.c_int32, dp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
@@ -176,6 +177,15 @@ def fast_plan_stats(nodes, targets, degree: int, theta: float):
     _check(lib.hobi_fast_plan_stats(y.ctypes.data, y.shape[0], x.ctypes.data, x.shape[0], int(degree), float(theta),
                                     C.byref(d), C.byref(a), C.byref(b), C.byref(p)))
     return {"direct_pairs": d.value, "approx_pairs": a.value, "batches": b.value, "proxy_clusters": p.value}
+
+
+def fp64_pair_functions(x):
+    """The FP64 far field's own 1/sqrt(x) and exp(-x) at host points x >= 0 (on the current GPU)."""
+    lib = load_library()
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    rs, ex = np.empty_like(x), np.empty_like(x)
+    _check(lib.hobi_fp64_pair_functions(x.ctypes.data, x.size, rs.ctypes.data, ex.ctypes.data))
+    return rs, ex
 
 
 class Solver:

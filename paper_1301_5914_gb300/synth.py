@@ -22,6 +22,7 @@ seen from outside (outward normals by the right-hand rule).
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -205,16 +206,16 @@ def _density_grid(centers, radii, lo, shape, h):
     return rho - 1.0
 
 
-def _density_points(P, centers, radii):
-    """rho(P) and grad rho(P) using a cell list over the atoms (cutoff 4 R)."""
+def _density_points_chunk(P, centers, radii, atoms):
     from scipy.spatial import cKDTree
 
+
     rmax = float(radii.max()) * np.sqrt(_CUT2)
-    tree = cKDTree(centers)
-    lists = tree.query_ball_point(P, rmax)
-    cnt = np.fromiter((len(l) for l in lists), dtype=np.int64, count=len(lists))
-    ip = np.repeat(np.arange(P.shape[0]), cnt)
-    ia = np.fromiter((j for l in lists for j in l), dtype=np.int64, count=int(cnt.sum()))
+    # every (point, atom) pair within rmax, in point order and then atom order
+    pairs = cKDTree(P).sparse_distance_matrix(atoms, rmax, output_type="ndarray")
+    order = np.lexsort((pairs["j"], pairs["i"]))
+    ip = pairs["i"][order].astype(np.int64)
+    ia = pairs["j"][order].astype(np.int64)
     d = P[ip] - centers[ia]
     inv_r2 = 1.0 / radii[ia] ** 2
     t = np.einsum("ij,ij->i", d, d) * inv_r2
@@ -223,6 +224,24 @@ def _density_points(P, centers, radii):
     coef = -2.0 * _BETA * inv_r2 * g
     grad = np.stack([np.bincount(ip, weights=coef * d[:, k], minlength=P.shape[0]) for k in range(3)], 1)
     return rho, grad
+
+
+def _density_points(P, centers, radii, chunk=4096):
+    """rho(P) and grad rho(P) over the atoms within the cutoff (4 R) of each point. Points are
+    processed in chunks on a thread pool; each point's sum runs over its atoms in index order, so
+    the result does not depend on the chunking or the thread count."""
+    import concurrent.futures as cf
+
+    from scipy.spatial import cKDTree
+
+    atoms = cKDTree(centers)
+    n = P.shape[0]
+    if n <= chunk:
+        return _density_points_chunk(P, centers, radii, atoms)
+    parts = [(a, min(n, a + chunk)) for a in range(0, n, chunk)]
+    with cf.ThreadPoolExecutor(max_workers=min(len(parts), os.cpu_count() or 1)) as ex:
+        res = list(ex.map(lambda ab: _density_points_chunk(P[ab[0]:ab[1]], centers, radii, atoms), parts))
+    return np.concatenate([r[0] for r in res]), np.concatenate([r[1] for r in res])
 
 
 def _density(points: np.ndarray, centers: np.ndarray, radii: np.ndarray):
