@@ -62,11 +62,22 @@ MOLECULE = {"eps1": 2.0, "eps2": 80.0, "kappa": 0.1257, "gmres_tol": 1e-6,
 # 6 for d and r^2, 3 for d.m, 3 for 1/r^2, 1/r^3 and v, 2 for 1 + kappa r and the exp2 argument,
 # 1 for P - 1, 4 for row 1, 3 for S, 2 for the 1/r^3 factors, 6 for the vector accumulation)
 OPS_PER_PAIR = 30
+OPS_PER_PAIR_ROW1 = 18  # row 1 only (reaction potential, energy): d, r^2, d.m, 1/r^2, v, 1 + kappa r,
+#                        the exp2 argument, P - 1 and the 4 operations of row 1
 MUFU_PER_PAIR = 2  # rsqrt.approx + ex2.approx
-# XU (MUFU) issue rate per SM per clock, from the far-field capture's counters: 0.217 XU warp
-# instructions per cycle per SM were 22.5 % of sm__inst_executed_pipe_xu's peak, i.e. about one
-# warp instruction (32 lanes) per cycle per SM.
-MUFU_LANES_PER_SM = 32
+# MUFU (XU) lanes per SM per clock: an rsqrt.approx.f32 throughput microbenchmark (independent
+# chains, CUDA events) measured 15.9 lane-operations per SM per clock on GB300 at 2070 MHz.
+MUFU_LANES_PER_SM = 16
+# FP64 far field (kappa > 0, both rows): FP64-pipe operations per pair as written: 3 for d, 3 for
+# r^2, 5 for the Newton step of 1/r, 1 for r, 1 for the exp argument, 3 for its reduction, 4 for its
+# polynomial, 1 for the table product, 2 for P - 1, 3 for d.m, 2 for 1/r^2 and v, 4 for row 1 and
+# 12 for row 2 (S, 1/r^3, the two factors, the vector accumulation).
+FP64_OPS_PER_PAIR = 44
+# FP64-pipe lanes per SM per clock: the nominal 1.25 TFLOP/s FP64 rate of GB300 is 0.625e12 FMA per
+# second = 2 lanes per SM per clock at 152 SMs x 2070 MHz. (ncu on the FP64 far field: 1.70 FP64
+# thread instructions per SM per cycle with sm__pipe_fp64_cycles_active at 88.9 % of peak, i.e. a
+# pipe peak of about 1.9.)
+FP64_LANES_PER_SM = 2.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "farfield32_c2_ico6_traffic.txt")
 FARFIELD_SRC = [os.path.join(ROOT, "paper_1301_5914_gb300", "csrc", f) for f in ("k_farfield.cu", "ff_body.cuh")]
 
@@ -368,6 +379,158 @@ def fast_summation_batch(hobi, mols, arrays, e1, e2, ka, tol, stream, degree, th
             "iterations_fast_minus_direct_max": int(np.max(np.abs(np.asarray(f["it"]) - np.asarray(d["it"]))))}
 
 
+def ff_launch_rate(prof):
+    """Average duration (s) and pair evaluations of the profiled far-field launches."""
+    n = max(int(prof["launches"]), 1)
+    return prof["farfield_ms"] / n / 1e3, prof["pairs"] / n
+
+
+def alu_fraction(launch_s, pairs_per_launch, ops_per_pair, lanes_per_sm, sms, f_mhz):
+    """Achieved lane operations per second of one kernel and its fraction of SMs x lanes x clock."""
+    achieved = pairs_per_launch * ops_per_pair / launch_s
+    peak = sms * lanes_per_sm * f_mhz * 1e6
+    return achieved, peak, achieved / peak
+
+
+def _dev(arrays, dev):
+    import torch
+
+    return tuple(torch.as_tensor(a, device=dev) for a in arrays)
+
+
+def extra_workload(hobi, name, dev, stream, sms, fmax, fp64_sample=4):
+    """One more BASELINE configuration, measured outside the timed region: its FP32 far-field rate
+    and lane-peak fraction in a GMRES solve to 1e-6, the solve time, and the FP32-bulk solution
+    against the FP64 operator's (mixed-precision refinement to 1e-10 on the FP64 far field; for a
+    batch, on `fp64_sample` sampled molecules). Plain FP64 GMRES on these sizes runs for minutes
+    and is not repeated here."""
+    import numpy as np
+    import torch
+
+    t0 = time.perf_counter()
+    cfg, mols = make_workload(name)
+    gen_s = time.perf_counter() - t0
+    e1, e2, ka, tol = cfg["eps1"], cfg["eps2"], cfg["kappa"], cfg["gmres_tol"]
+    rec = {k: cfg[k] for k in ("workload", "n_faces", "n_vertices", "n_nodes", "n_charges") if k in cfg}
+    rec["generate_s"] = gen_s
+    rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    relmax = lambda a, b: float(torch.max(torch.abs(a - b)) / torch.max(torch.abs(b)))
+    if len(mols) == 1:
+        s = hobi.Solver(*_dev(mols[0], dev), e1, e2, ka, precision="fp32", stream=stream)
+        s.profile_enable(True)
+        phi, dphi, info = s.solve(tol, 400)
+        prof = s.profile_read()
+        E32 = s.energy()
+        _, _, ir = s.solve_refined(1e-10, 8, 400)
+        u64 = s.solution()
+        E64 = s.energy()
+        s.close()
+        nv = phi.numel()
+        acc = {"phi_rel_l2": rel(phi, u64[:nv]), "phi_rel_max": relmax(phi, u64[:nv]),
+               "dphi_rel_l2": rel(dphi, u64[nv:]), "E_sol_fp32": E32, "E_sol_fp64_operator": E64,
+               "E_rel": abs(E32 - E64) / abs(E64), "reference": "FP64-operator solution (refinement to 1e-10)",
+               "reference_s": ir["solve_ms"] / 1e3, "reference_fp64_residual": ir["rel_residual"]}
+        gm = {"fp32_bulk_s": info["solve_ms"] / 1e3, "iterations": info["iterations"]}
+    else:
+        arrays = _dev([np.concatenate([np.asarray(m[k]).reshape(-1, 4 if k == 3 else 3) for m in mols]).astype(
+            np.int32 if k == 1 else np.float64) for k in range(4)], dev)
+        b = hobi.BatchSolver(mols, e1, e2, ka, precision="fp32", device_arrays=arrays, stream=stream)
+        b.profile_enable(True)
+        phis, dphis, info = b.solve(tol, 400)
+        prof = b.profile_read()
+        E32 = np.asarray(b.energy())
+        b.close()
+        order = np.argsort([m[1].shape[0] for m in mols])
+        sample = [int(order[i]) for i in np.linspace(0, len(mols) - 1, fp64_sample).round().astype(int)]
+        worst = {"phi_rel_l2": 0.0, "phi_rel_max": 0.0, "dphi_rel_l2": 0.0, "E_rel": 0.0}
+        for m in sample:
+            s = hobi.Solver(*_dev(mols[m], dev), e1, e2, ka, precision="fp32", stream=stream)
+            s.solve_refined(1e-10, 8, 400)
+            u64 = s.solution()
+            E64 = s.energy()
+            s.close()
+            nv = mols[m][0].shape[0]
+            p32, d32 = torch.as_tensor(phis[m], device=dev), torch.as_tensor(dphis[m], device=dev)
+            for k, v in (("phi_rel_l2", rel(p32, u64[:nv])), ("phi_rel_max", relmax(p32, u64[:nv])),
+                         ("dphi_rel_l2", rel(d32, u64[nv:])), ("E_rel", abs(E32[m] - E64) / abs(E64))):
+                worst[k] = max(worst[k], v)
+        acc = dict(worst, reference=f"FP64-operator solutions (refinement to 1e-10) of molecules {sample}, "
+                                    "worst of them")
+        its = info["iterations"].tolist()
+        gm = {"fp32_bulk_s": info["solve_ms"] / 1e3, "iterations_min_max": [int(min(its)), int(max(its))],
+              "n_molecules": len(mols)}
+    launch_s, pairs = ff_launch_rate(prof)
+    ach, peak, frac = alu_fraction(launch_s, pairs, OPS_PER_PAIR, 128, sms, fmax)
+    rec.update(farfield={"kernel": "k_farfield_batch32" if len(mols) > 1 else "k_farfield32<ROW2=true>",
+                         "pairs_per_s": pairs / launch_s, "avg_launch_ms": launch_s * 1e3, "launches": prof["launches"],
+                         "frac_fp32_lane_peak": frac, "mufu_frac": pairs * MUFU_PER_PAIR / launch_s / (sms * MUFU_LANES_PER_SM * fmax * 1e6)},
+               gmres_fp32_bulk=gm, accuracy_fp32_vs_fp64_operator=acc,
+               fp64_plain="not run: plain FP64 GMRES on this size takes minutes")
+    return rec
+
+
+def lobi_object(hobi, arrays, e1, e2, ka, tol, stream, sms, fmax):
+    """LOBI-PB (the paper's low-order scheme) on the same surface: its self-skipping FP32 far field
+    (N_f targets x N_f sources per matvec) and its GMRES to 1e-6."""
+    import numpy as np
+    import torch
+
+    s = hobi.Solver(*arrays, e1, e2, ka, precision="fp32", scheme="lobi", stream=stream)
+    u = torch.as_tensor(np.random.default_rng(0).normal(size=2 * s.npts), device=arrays[0].device)
+    s.profile_enable(True)
+    for _ in range(3):
+        s.matvec(u)
+    s.profile_read()
+    for _ in range(10):
+        s.matvec(u)
+    launch_s, pairs = ff_launch_rate(s.profile_read())
+    _, _, frac = alu_fraction(launch_s, pairs, OPS_PER_PAIR, 128, sms, fmax)
+    phi, dphi, info = s.solve(tol, 400)
+    E = s.energy()
+    s.close()
+    return {"scheme": "LOBI-PB (flat faces, centroid collocation, self term dropped)", "n_unknowns": 2 * s.npts,
+            "pairs_per_matvec": pairs, "farfield_ms": launch_s * 1e3, "pairs_per_s": pairs / launch_s,
+            "frac_fp32_lane_peak": frac, "ops_per_pair": f"{OPS_PER_PAIR} FP32 FMA-pipe + zero-distance select",
+            "gmres_fp32_bulk_s": info["solve_ms"] / 1e3, "iterations": info["iterations"], "E_sol": E}
+
+
+def reaction_object(hobi, arrays, e1, e2, ka, tol, stream, sms, fmax, n_points=16384, radius=8.0):
+    """Off-surface output: the reaction potential at n_points interior points from a solved handle,
+    FP32-bulk and FP64 (row-1 far field, N_points x N_nodes pairs per call)."""
+    import numpy as np
+    import torch
+
+    from paper_1301_5914_gb300 import synth
+
+    pts = torch.as_tensor(synth.ball_charges(n_points, radius, 77)[:, :3].copy(), device=arrays[0].device)
+    s = hobi.Solver(*arrays, e1, e2, ka, precision="fp32", stream=stream)
+    s.solve(tol, 400)
+    out = {"n_points": n_points, "points": f"uniform in the r <= {radius} A ball, seed 77"}
+    for prec, ops, lanes in (("fp32", OPS_PER_PAIR_ROW1, 128), ("fp64", None, FP64_LANES_PER_SM)):
+        s.set_precision(prec)
+        s.profile_enable(True)
+        for _ in range(2):
+            s.reaction_potential(pts)
+        s.profile_read()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        reps = 5 if prec == "fp32" else 2
+        ev[0].record(stream)
+        for _ in range(reps):
+            phi = s.reaction_potential(pts)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        launch_s, pairs = ff_launch_rate(s.profile_read())
+        rec = {"call_ms": ev[0].elapsed_time(ev[1]) / reps, "farfield_ms": launch_s * 1e3, "pairs_per_s": pairs / launch_s}
+        if ops:
+            rec["frac_fp32_lane_peak"] = alu_fraction(launch_s, pairs, ops, lanes, sms, fmax)[2]
+        out[prec] = rec
+        if prec == "fp32":
+            phi32 = phi.clone()
+    out["fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(phi32 - phi) / torch.linalg.norm(phi))
+    s.close()
+    return out
+
+
 def run_ours(args):
     cfg, mols = make_workload(args.workload)  # before any CUDA call (the c4 generator uses a spawn pool)
     import numpy as np
@@ -402,15 +565,18 @@ def run_ours(args):
         return hobi.Solver(Vd, Fd, Nd, Qd, e1, e2, ka, precision=precision, stream=stream)
 
     def step(profile: bool, precision="fp32", host=False):
+        """setup + solve + energy; with profile, the far-field launches of the solve (the matvecs)
+        and those of the energy are read separately."""
         s = make(precision, host)
         if profile:
             s.profile_enable(True)
         phi, dphi, info = s.solve(tol, 400)
-        E = s.energy()
         prof = s.profile_read() if profile else None
+        E = s.energy()
+        prof_e = s.profile_read() if profile else None
         n_launch = s.kernel_launches()
         s.close()
-        return info, E, prof, n_launch, phi, dphi
+        return info, E, prof, prof_e, n_launch, phi, dphi
 
     for _ in range(args.warmup):
         step(False)
@@ -426,15 +592,16 @@ def run_ours(args):
         flush.zero_()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        info, E, prof, nl, _, _ = step(True)
+        info, E, prof, prof_e, nl, _, _ = step(True)
         ev1.record(stream)
         torch.cuda.synchronize()
         times.append(ev0.elapsed_time(ev1))
         ff_ms += prof["farfield_ms"]
         ff_launch += prof["launches"]
         ff_pairs += prof["pairs"]
-        # single: the profile includes the energy launch; batch: energies run per molecule
-        pairs_step.append(prof["pairs"] + (energy_pairs if batched else 0.0))
+        # single molecule: the energy's far-field launch is profiled on its own; a batch computes
+        # its energies per molecule (not profiled), so their pairs are counted from the sizes
+        pairs_step.append(prof["pairs"] + (energy_pairs if batched else prof_e["pairs"]))
         launches += nl
         iters.append(info["iterations"].tolist() if batched else info["iterations"])
     torch.cuda.synchronize()
@@ -447,7 +614,8 @@ def run_ours(args):
     value, ms_per_step = aggregate(per_rank, pairs_per_step, args.steps)
 
     if rank == 0:
-        # roofline of the dominant kernel (far field, FP32 bulk, both rows), live CUDA-event timing
+        # roofline of the dominant kernel: the far field of the GMRES matvecs (FP32 bulk, both rows),
+        # live CUDA-event timing of those launches only (the energy launch is reported apart)
         props = torch.cuda.get_device_properties(dev)
         sms = props.multi_processor_count
         try:
@@ -455,7 +623,7 @@ def run_ours(args):
             fmax = float(peaks.get("sm_max_mhz", 2070.0))
             peak_src = "MEASURED_PEAKS.json sm_max_mhz"
         except (OSError, ValueError):
-            fmax, peak_src = 2070.0, "nominal max SM clock"
+            fmax, peak_src = 2070.0, "nominal maximum SM clock (MEASURED_PEAKS.json absent)"
         peak = sms * 128 * fmax * 1e6 / 1e9  # Ginst/s, FP32 FMA-pipe lanes
         avg_launch_s = ff_ms / ff_launch / 1e3
         pairs_per_launch = ff_pairs / ff_launch
@@ -464,25 +632,38 @@ def run_ours(args):
         fobs = clk.get("sm_mhz") or fmax
         roof = {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginst/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_farfield_batch32" if batched else "k_farfield32<ROW2=true>",
+            "traffic": traffic, "kernel": "k_farfield32<ROW2=true>" if not batched else "k_farfield_batch32",
             "algorithmic": f"{OPS_PER_PAIR} FP32 FMA-pipe instructions + {MUFU_PER_PAIR} MUFU per pair",
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src})",
             "pairs_per_s": pairs_per_launch / avg_launch_s,
             "avg_launch_ms": avg_launch_s * 1e3,
+            "launches_per_step": ff_launch / args.steps,
             "frac_at_median_clock": achieved / (sms * 128 * fobs * 1e6 / 1e9),
             "mufu_frac": pairs_per_launch * MUFU_PER_PAIR / avg_launch_s / (sms * MUFU_LANES_PER_SM * fmax * 1e6),
+            "mufu_basis": f"{sms} SMs x {MUFU_LANES_PER_SM} MUFU lanes (rsqrt.approx.f32 microbenchmark) x {fmax:.0f} MHz",
             "farfield_share_of_step": ff_ms / total_ms,
         }
-        # FP64 plain path on the same inputs (outside the timed region): GMRES time to 1e-6
+        if not batched:
+            roof["energy_launch_ms"] = prof_e["farfield_ms"] / max(prof_e["launches"], 1)
+        # FP64 plain path on the same inputs (outside the timed region): GMRES time to 1e-6 and the
+        # roofline of its far-field kernel
         gm = {"fp32_bulk_s": None, "fp64_plain_s": None}
         acc = {}
+        fp64_roof = None
         if not args.no_fp64:
-            i64, E64, _, _, p64, d64 = step(False, "fp64")
-            i32, E32, _, _, p32, d32 = step(False, "fp32")
+            i64, E64, p64prof, _, _, p64, d64 = step(True, "fp64")
+            i32, E32, _, _, _, p32, d32 = step(False, "fp32")
             it32 = i32["iterations"].tolist() if batched else i32["iterations"]
             it64 = i64["iterations"].tolist() if batched else i64["iterations"]
             gm = {"fp32_bulk_s": i32["solve_ms"] / 1e3, "fp64_plain_s": i64["solve_ms"] / 1e3,
                   "iterations_fp32": it32, "iterations_fp64": it64, "speedup": i64["solve_ms"] / i32["solve_ms"]}
+            l64, pr64 = ff_launch_rate(p64prof)
+            a64, pk64, f64 = alu_fraction(l64, pr64, FP64_OPS_PER_PAIR, FP64_LANES_PER_SM, sms, fmax)
+            fp64_roof = {"bound": "alu", "kernel": "k_farfield64<ROW2=true>" if not batched else "k_farfield_batch64",
+                         "achieved": a64 / 1e9, "peak": pk64 / 1e9, "unit": "Ginst/s", "frac": f64,
+                         "algorithmic": f"{FP64_OPS_PER_PAIR} FP64-pipe instructions + 1 MUFU (rsqrt seed) per pair",
+                         "peak_basis": f"{sms} SMs x {FP64_LANES_PER_SM:g} FP64 lanes (nominal 1.25 TFLOP/s) x {fmax:.0f} MHz",
+                         "pairs_per_s": pr64 / l64, "avg_launch_ms": l64 * 1e3}
             if not batched:  # mixed precision: FP32-bulk corrections, tolerance met on the FP64 operator
                 for rtol in (tol, 1e-10):
                     sr = make("fp32")
@@ -515,15 +696,20 @@ def run_ours(args):
             else:
                 fast = fast_summation(hobi, (Vd, Fd, Nd, Qd), e1, e2, ka, tol, stream, args.fast_degree,
                                       args.fast_theta)
+        # the paper's low-order scheme and the off-surface output on the same surface
+        lobi = reaction = None
+        if not batched and not args.no_extra:
+            lobi = lobi_object(hobi, (Vd, Fd, Nd, Qd), e1, e2, ka, tol, stream, sms, fmax)
+            reaction = reaction_object(hobi, (Vd, Fd, Nd, Qd), e1, e2, ka, tol, stream, sms, fmax)
         # end to end through the public API with host buffers, copies inside the timed region
         e2e_t, e2e_pairs = [], []
         for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            inf, _, prof, _, _, _ = step(True, "fp32", host=True)
+            inf, _, prof, prof_e, _, _, _ = step(True, "fp32", host=True)
             e2e_t.append(time.perf_counter() - t0)
-            e2e_pairs.append(prof["pairs"] + (energy_pairs if batched else 0.0))
+            e2e_pairs.append(prof["pairs"] + (energy_pairs if batched else prof_e["pairs"]))
         h2d = Vh.nbytes + Fh.nbytes + Nh.nbytes + Qh.nbytes
         d2h = 2 * Vh.shape[0] * 8 + 8 * len(mols)
         e2e = {"value": sum(e2e_pairs) / sum(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -542,6 +728,13 @@ def run_ours(args):
                    "sample_1_thread": f"{max(8, args.cpu_rows // 16)} rows ({pairs1:.3g} pairs, {dt1:.1f} s)",
                    # the oracle's time for the whole timed step at its measured rate (pairs / rate)
                    "step_s_extrapolated": pairs_per_step / val}
+        # the larger BASELINE configurations (outside the timed region)
+        extra = None
+        if args.workload == "c2l6" and not args.no_extra and ws == 1:
+            extra = {}
+            for name in args.extra.split(","):
+                if name:
+                    extra[name] = extra_workload(hobi, name, dev, stream, sms, fmax)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -551,7 +744,8 @@ def run_ours(args):
                            pairs_per_step=pairs_per_step, gmres_iterations=iters[-1],
                            E_sol=(E.tolist() if batched else E)),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "gmres": gm, "accuracy": acc, "phases": phases, "fast_summation": fast,
+            "gmres": gm, "fp64_roofline": fp64_roof, "accuracy": acc, "phases": phases, "fast_summation": fast,
+            "lobi": lobi, "reaction_potential": reaction, "workloads": extra,
         }
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -570,6 +764,9 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain GMRES comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fast", action="store_true", help="skip the fast-summation (treecode) comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the LOBI-PB, off-surface potential and larger-workload objects")
+    ap.add_argument("--extra", default="c5,c4", help="larger workloads measured after the default one")
     ap.add_argument("--fast-degree", type=int, default=5)
     ap.add_argument("--fast-theta", type=float, default=0.7)
     ap.add_argument("--cpu-rows", type=int, default=1024)

@@ -4,11 +4,11 @@
  * The library solves the well-posed boundary integral form of the linear
  * Poisson-Boltzmann equation (W. Geng, "Parallel Higher-order Boundary
  * Integral Electrostatics Computation on Molecular Surfaces with Curved
- * Triangulation", Sec. 2.1, Eqs. eqbim_3/eqbim_4) on a closed triangulated
+ * Triangulation", Sec. 2.1, Eqs. (8)/(9)) on a closed triangulated
  * molecular surface, with curved elements built from vertex normals
  * (Sec. 2.2), 4-point quadrature on regular triangles, 16-point regularised
  * Gauss-Legendre quadrature on singular triangles (Sec. 2.3), GMRES, and the
- * electrostatic solvation energy (Sec. 2.5, Eq. solvation_energy).
+ * electrostatic solvation energy (Sec. 2.5, Eq. (23)).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -22,7 +22,7 @@
  *    units of the formulation (G = 1/(4 pi r)); multiply by HOBI_KCAL_PER_MOL_E
  *    for kcal/(mol e). Energies are kcal/mol.
  *  - Dielectric ratio: eps = eps2/eps1 (the paper prints eps1/eps2 after
- *    Eq_Ls; only eps2/eps1 makes eqbim_3/eqbim_4 consistent with the jump
+ *    Eq. (10); only eps2/eps1 makes Eqs. (8)/(9) consistent with the jump
  *    condition). Source terms carry 1/eps1.
  *  - Array arguments (vertices, faces, normals, charges, u, Au, phi, dphi,
  *    points, potentials) are HOST pointers when opt.mem_device == 0 and
@@ -69,7 +69,7 @@ typedef enum {
   HOBI_SCHEME_HOBI = 0, /* curved elements, 4-point regular + 16-point singular rules, unknowns at the
                            N_v vertices (Sec. 2.2-2.3) */
   HOBI_SCHEME_LOBI = 1  /* the paper's low-order comparison scheme LOBI-PB (Sec. 2.4, Eqs.
-                           eqdbef1/eqdbef2): flat triangles, centroid collocation, the singular
+                           (21)/(22)): flat triangles, centroid collocation, the singular
                            (self) triangle dropped; unknowns at the N_f centroids, normals are the
                            flat face normals (vertex_normals are only validated) */
 } hobi_scheme;
@@ -129,7 +129,7 @@ void hobi_default_options(hobi_options* opt);
  * finite non-zero normals) and returns HOBI_ERR_MESH with a message otherwise.
  * Copies every input into library-owned device memory; the caller may free its arrays on
  * return. Then builds the curved elements and quadrature nodes, the vertex-to-face adjacency,
- * the singular-triangle correction table and the right-hand side [S1; S2] (Eq_Ss).
+ * the singular-triangle correction table and the right-hand side [S1; S2] (Eq. (11)).
  * On success *out owns all device memory until hobi_destroy. */
 int hobi_setup(const double* vertices, int64_t n_v, const int32_t* faces, int64_t n_f,
                const double* vertex_normals, const double* charges, int64_t n_c, double eps1,
@@ -143,11 +143,11 @@ int hobi_set_precision(hobi_t h, int32_t precision);
  * source quadrature nodes (4 N_f for HOBI, N_f for LOBI). */
 int hobi_sizes(hobi_t h, int64_t* n_v, int64_t* n_f, int64_t* n_c, int64_t* n_nodes, int64_t* n_points);
 
-/* One discrete operator application Au = A u (Eqs. eqdbef3-eqdbef6): u and Au are 2 n_v
+/* One discrete operator application Au = A u (Eqs. (17)-(20)): u and Au are 2 n_v
  * doubles (layout above). Au must not alias u. */
 int hobi_matvec(hobi_t h, const double* u, double* Au);
 
-/* Right-hand side b = [S1; S2] at the vertices (Eq_Ss), 2 n_v doubles. */
+/* Right-hand side b = [S1; S2] at the vertices (Eq. (11)), 2 n_v doubles. */
 int hobi_rhs(hobi_t h, double* b);
 
 /* Solve A u = b by GMRES from u = 0 (restart opt.restart) until ||b - A u||/||b|| <= tol or
@@ -185,40 +185,44 @@ int hobi_set_solution(hobi_t h, const double* u);
 int hobi_get_solution(hobi_t h, double* u);
 
 /* Reaction potential phi_reac at n_points points inside the molecule (the integral part of
- * Eq. solvation_energy, regular rule on every element), from the handle's solution.
+ * Eq. (23), regular rule on every element), from the handle's solution.
  * points [n_points][3], phi [n_points] (formulation units). */
 int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, double* phi);
 
 /* Same result as hobi_reaction_potential, but the call allocates no device memory. The paper
- * has no counterpart: this entry point serves callers that cannot allocate at call time (code
- * running while a stream is captured into a CUDA graph, code that must avoid the device-wide
- * synchronisation an allocation can cause, hosts whose device memory belongs to another
- * allocator). Create the handle (hobi_setup) beforehand; this call then uses the handle's
- * tables plus one file-scope device array of 2.5 MiB that every GPU loading the library keeps
- * until process exit.
+ * has no counterpart. It is meant for callers that must not allocate once they are running: a
+ * host whose device memory is owned by another allocator (a framework's caching pool holding the
+ * GPU's free memory, where a cudaMalloc from this library would fail or upset the pool's
+ * accounting), a service whose device-memory footprint is fixed at start-up, or a latency-bound
+ * loop that cannot pay cudaMalloc's cost and its synchronisation with the device's other streams.
+ * Create the handle (hobi_setup) beforehand; this call then uses the handle's tables plus one
+ * file-scope device array of 2.5 MiB that every GPU loading the library keeps until process exit.
  *   n_points <= 4096 per call; larger requests return HOBI_ERR_ARG (split them, or use
- *   hobi_reaction_potential). points/phi follow opt.mem_device like every array argument.
- *   The first call on each device looks up the array's device address (cudaGetSymbolAddress);
- *   make that first call before any stream capture.
- *   The array is shared by every call on a device and keeps the last call's contents: calls
- *   that overlap on the GPU (different streams or handles on one device) race on it.
+ *   hobi_reaction_potential). n_points == 0 returns HOBI_OK and touches nothing.
+ *   points/phi follow opt.mem_device like every array argument.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *   and keeps it for the later calls.
+ *   The array is shared by every call on a device and keeps the last call's contents (each call
+ *   overwrites every entry it reads, so nothing needs clearing): calls that overlap on the GPU
+ *   (different streams or handles on one device) race on it.
+ *   With hobi_profile_enable on, its far-field launch is timed like the others.
  * Results equal hobi_reaction_potential's up to summation order (at most 64 source chunks). */
 int hobi_reaction_potential_noalloc(hobi_t h, const double* points, int64_t n_points, double* phi);
 
 /* Electrostatic solvation energy E_sol = (1/2) sum_k q_k phi_reac(x_k) in kcal/mol
- * (Eq. solvation_energy) from the handle's solution; requires hobi_solve or
+ * (Eq. (23)) from the handle's solution; requires hobi_solve or
  * hobi_set_solution first (else HOBI_ERR_STATE). e_sol is a host pointer. */
 int hobi_energy(hobi_t h, double* e_sol);
 
 /* Debug/parity accessors (host or device pointers per mem_device, FP64):
  * quadrature nodes of the regular rule, [n_f][4][3] each: position y_{j,m}, unit normal
- * nu_{j,m}, and W_{j,m,n} = w_m J_{j,m} L_n(r_m, s_m) (Sec. 2.2, eqdbef3). */
+ * nu_{j,m}, and W_{j,m,n} = w_m J_{j,m} L_n(r_m, s_m) (Sec. 2.2, Eq. (17)). */
 int hobi_get_nodes(hobi_t h, double* y, double* nu, double* W);
 
 /* Singular-triangle correction table: one entry per (vertex i, face j incident to i), in
  * vertex order then ascending face index. For entry e: vertex[e] = i, face[e] = j, and
  * coeff[e][n][k] (k = K1..K4) = (16-point singular rule) - (4-point regular rule) of
- * sum_m W_{j,m,n} K_k(x_i, y_{j,m}) (Sec. 2.3, eqdbef5/eqdbef6 minus eqdbef3/eqdbef4).
+ * sum_m W_{j,m,n} K_k(x_i, y_{j,m}) (Sec. 2.3, Eqs. (19)/(20) minus Eqs. (17)/(18)).
  * Call with all three arrays NULL to get *n_entries first. Arrays are HOST pointers. */
 int hobi_get_correction(hobi_t h, int64_t* n_entries, int32_t* vertex, int32_t* face,
                         double* coeff);
@@ -260,10 +264,10 @@ int hobi_fast_plan_stats(const double* nodes, int64_t n_nodes, const double* tar
 
 /* Accuracy accessor of the FP64 far field's own pair functions, evaluated on the current CUDA
  * device: rsqrt_x[k] = 1/sqrt(x[k]) (MUFU seed + one Newton step) and exp_neg_x[k] = exp(-x[k])
- * (64-entry table of 2^(j/64) + degree-5 polynomial), exactly as the FP64 kernels compute
- * 1/r and e^{-kappa r} (kernels of Eq. (10) in the paper). x: n host doubles, finite and >= 0
- * (x = 0 gives rsqrt inf); n <= 2^24. All three arrays are HOST arrays. Allocates and frees
- * temporary device memory. */
+ * (256-entry table of 2^(j/256) + degree-4 polynomial), exactly as the FP64 kernels compute
+ * 1/r and e^{-kappa r} (kernels of Eq. (10) in the paper). x: n host doubles in [0, 1e12]
+ * (x = 0 gives rsqrt inf; far-field arguments stay below 1e7); n <= 2^24. All three arrays
+ * are HOST arrays. Allocates and frees temporary device memory. */
 int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x);
 
 /* Free every resource of the handle (NULL is a no-op). */
@@ -274,7 +278,7 @@ void hobi_destroy(hobi_t h);
  * runs one far-field launch over a task list covering every unconverged molecule,
  * and the Arnoldi/Givens work of all molecules in one set of launches (replayed as a CUDA
  * graph); converged molecules drop out. Each molecule follows exactly the single-molecule
- * method above (Sec. 2.2-2.3, Eqs. eqdbef3-eqdbef6), with its own Krylov space, residual
+ * method above (Sec. 2.2-2.3, Eqs. (17)-(20)), with its own Krylov space, residual
  * test and restart.
  * ------------------------------------------------------------------------------------- */
 typedef struct hobi_batch_ctx* hobi_batch_t;
@@ -307,7 +311,7 @@ int hobi_matvec_batch(hobi_batch_t b, const double* u, double* Au);
 int hobi_solve_batch(hobi_batch_t b, double tol, int32_t max_it, double* phi, double* dphi,
                      int32_t* iterations, int32_t* status, hobi_solve_info* info);
 
-/* Solvation energy of every molecule (Eq. solvation_energy), e_sol[n_mol] HOST, kcal/mol. */
+/* Solvation energy of every molecule (Eq. (23)), e_sol[n_mol] HOST, kcal/mol. */
 int hobi_energy_batch(hobi_batch_t b, double* e_sol);
 
 /* Timing of the batched far-field launches, as hobi_profile_enable / hobi_profile_read

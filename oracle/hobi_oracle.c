@@ -9,16 +9,16 @@
  * or constant generators.
  *
  * Everything is IEEE double. The code follows the paper's steps in order:
- *   Sec. 2.1  well-posed equations eqbim_3/eqbim_4, kernels K1..K4 and
- *             sources S1,S2 (Eq_Ls, Eq_Ss);
- *   Sec. 2.2  cubic edge arcs, the (r,s)->(u,v) map (eqrs2uv), the 10-point
- *             cubic interpolant (eqintepolation), the curved-element
+ *   Sec. 2.1  well-posed equations Eqs. (8)/(9), kernels K1..K4 and
+ *             sources S1,S2 (Eq. (10), Eq. (11));
+ *   Sec. 2.2  cubic edge arcs, the (r,s)->(u,v) map (Eq. (14)), the 10-point
+ *             cubic interpolant (Eq. (15)), the curved-element
  *             quadrature with Jacobian, the 4-point regular rule and the
- *             regular matvec terms (eqdbef3/eqdbef4);
+ *             regular matvec terms (Eqs. (17)/(18));
  *   Sec. 2.3  the Duffy map r=(1-y)x, s=yx with 4x4 Gauss-Legendre on
- *             singular triangles (eqdbef5/eqdbef6);
- *   Sec. 2.5  the solvation energy (solvation_energy);
- *   GMRES     (Sec. 1 abstract, Sec. 2.6 pseudocode tb_MPI steps 11-17).
+ *             singular triangles (Eqs. (19)/(20));
+ *   Sec. 2.5  the solvation energy (Eq. (23));
+ *   GMRES     (Sec. 1 abstract; the iteration loop of the Table 1 pseudocode, Sec. 2.6).
  *
  * Readings where the paper is silent or inconsistent (each listed in the
  * design notes): eps = eps2/eps1; S1,S2 carry 1/eps1; the diagonal term is
@@ -121,7 +121,7 @@ void or_singular_rule(double r[16], double s[16], double w[16]) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Cubic (P3) Lagrange basis on the 10-point triangle (eqintepolation) */
+/* Cubic (P3) Lagrange basis on the 10-point triangle (Eq. (15)) */
 /* ------------------------------------------------------------------ */
 /* Node order used throughout the oracle, by (r,s):
  *  0:(0,0)=X1  1:(1,0)=X2  2:(0,1)=X3
@@ -204,9 +204,9 @@ void or_edge_arc(const double* P, const double* nP, const double* Q, const doubl
   unit3(n);
 }
 
-/* The 10 interpolation points of one curved element (Sec. 2.2 steps 1-3):
+/* The 10 interpolation points of one curved element (Sec. 2.2, the 10-point construction):
  * vertices, two points on each edge arc at t = 1/3, 2/3, and the interior
- * point (r,s) = (1/3,1/3), i.e. (u,v) = (2/3,1/2) by eqrs2uv: the arc from
+ * point (r,s) = (1/3,1/3), i.e. (u,v) = (2/3,1/2) by Eq. (14): the arc from
  * Y1 = arc X1X2 at u to Y2 = arc X1X3 at u, evaluated at v. */
 void or_element_points(const double* X1, const double* n1, const double* X2, const double* n2,
                        const double* X3, const double* n3, double pts[10][3]) {
@@ -228,7 +228,7 @@ void or_element_points(const double* X1, const double* n1, const double* X2, con
 }
 
 /* Point, unit normal and area Jacobian |x_r x x_s| of the interpolated curved
- * element at (r,s) (eqintepolation and the curved-element quadrature rule). */
+ * element at (r,s) (Eq. (15) and the curved-element quadrature rule). */
 void or_element_eval(const double pts[10][3], double r, double s, double* x, double* nu, double* J) {
   double N[10], Nr[10], Ns[10];
   or_p3_basis(r, s, N, Nr, Ns);
@@ -246,7 +246,7 @@ void or_element_eval(const double pts[10][3], double r, double s, double* x, dou
 }
 
 /* ------------------------------------------------------------------ */
-/* Kernels (Eq_Ls)                                                     */
+/* Kernels (Eq. (10))                                                     */
 /* ------------------------------------------------------------------ */
 /* K1..K4 at target x (normal nx) and source y (normal ny):
  *   K1 = G0 - Gk,                 K2 = eps dGk/dny - dG0/dny,
@@ -314,7 +314,7 @@ or_ctx* or_create(const double* V, int64_t nv, const int32_t* F, int64_t nf, con
   or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
   c->nv = nv; c->nf = nf; c->nc = nc;
   c->eps1 = eps1; c->eps2 = eps2; c->kappa = kappa;
-  c->eps = eps2 / eps1; /* reading: eps = eps2/eps1 makes eqbim_3/4 consistent */
+  c->eps = eps2 / eps1; /* reading: eps = eps2/eps1 makes Eqs. (8)/(9) consistent */
   c->V = (double*)malloc(sizeof(double) * 3 * nv);
   c->Nv = (double*)malloc(sizeof(double) * 3 * nv);
   c->F = (int32_t*)malloc(sizeof(int32_t) * 3 * nf);
@@ -369,7 +369,7 @@ void or_get_nodes(const or_ctx* c, double* y, double* nu, double* W) {
 void or_get_element_points(const or_ctx* c, double* pts) { memcpy(pts, c->pts, sizeof(double) * 30 * c->nf); }
 
 /* Singular-triangle contribution to rows i and i+N_v from face j, of which
- * vertex i is a corner (Sec. 2.3, eqdbef5/eqdbef6). The element keeps its
+ * vertex i is a corner (Sec. 2.3, Eqs. (19)/(20)). The element keeps its
  * geometry in stored vertex order; the singular rule's (r',s') frame puts
  * vertex i at the origin through a cyclic relabelling of the barycentrics.
  * Returns the 2x2 coefficient blocks acting on (u_{N_v+v}, u_v) for the
@@ -428,7 +428,7 @@ int or_singular_coeffs_n(const or_ctx* c, int64_t i, int64_t j, int ngl, const d
   return 0;
 }
 
-/* One row pair of the matvec {Au}_i, {Au}_{i+N_v} (eqdbef3-eqdbef6, the
+/* One row pair of the matvec {Au}_i, {Au}_{i+N_v} (Eqs. (17)-(20), the
  * diagonal term counted once): regular faces with the 4-point rule, the
  * faces having vertex i as a corner with the 16-point singular rule. */
 static void matvec_row(const or_ctx* c, const double* u, int64_t i, const double* sr, const double* ss,
@@ -481,7 +481,7 @@ void or_matvec_rows(const or_ctx* c, const double* u, const int64_t* rows, int64
   for (int64_t k = 0; k < nrows; ++k) matvec_row(c, u, rows[k], sr, ss, sw, &out[2 * k], &out[2 * k + 1]);
 }
 
-/* Right-hand side b = [S1; S2] at the vertices (Eq_Ss, routine (1)), with the
+/* Right-hand side b = [S1; S2] at the vertices (Eq. (11), routine (1)), with the
  * 1/eps1 factor of the charge potential in Omega_1 (reading). */
 void or_rhs(const or_ctx* c, double* b) {
   const int64_t nv = c->nv;
@@ -504,7 +504,7 @@ void or_rhs(const or_ctx* c, double* b) {
 
 /* Reaction potential at the charge sites, phi_reac(x_k) = integral of
  * K1 dphi/dnu + K2 phi with the regular rule over every face
- * (solvation_energy, routine (6)). */
+ * (Eq. (23), routine (6)). */
 void or_reaction_potential(const or_ctx* c, const double* u, const double* pts, int64_t np, double* phi) {
   const int64_t nv = c->nv;
   double unused_nx[3] = {0.0, 0.0, 1.0}; /* K1, K2 do not use the target normal */
@@ -632,7 +632,7 @@ int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int resta
 }
 
 /* ------------------------------------------------------------------ */
-/* Low-order scheme, LOBI-PB (Sec. 2.4, eqdbef1/eqdbef2)               */
+/* Low-order scheme, LOBI-PB (Sec. 2.4, Eqs. (21)/(22))               */
 /* ------------------------------------------------------------------ */
 /* Flat triangles with centroid collocation: unknowns are phi and dphi/dnu at the
  * N_f centroids, each triangle contributes W_j = its area times the kernels at its
@@ -685,7 +685,7 @@ void or_lobi_matvec_rows(const or_ctx* c, const double* u, const int64_t* rows, 
   for (int64_t k = 0; k < nrows; ++k) lobi_row(c, u, rows[k], &out[2 * k], &out[2 * k + 1]);
 }
 
-/* Sources S1, S2 (Eq_Ss, with 1/eps1) at the centroids, face normals. */
+/* Sources S1, S2 (Eq. (11), with 1/eps1) at the centroids, face normals. */
 void or_lobi_rhs(const or_ctx* c, double* b) {
   const int64_t nf = c->nf;
 #pragma omp parallel for schedule(static)
@@ -705,7 +705,7 @@ void or_lobi_rhs(const or_ctx* c, double* b) {
   }
 }
 
-/* E_sol (kcal/mol) with the centroid rule for the reaction potential (solvation_energy). */
+/* E_sol (kcal/mol) with the centroid rule for the reaction potential (Eq. (23)). */
 double or_lobi_energy(const or_ctx* c, const double* u) {
   const int64_t nf = c->nf;
   double unused_nx[3] = {0.0, 0.0, 1.0}; /* K1, K2 do not use the target normal */

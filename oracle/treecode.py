@@ -1,7 +1,7 @@
 """Barycentric Lagrange treecode for the HOBI-PB far-field sum, in plain numpy FP64
 (test infrastructure only; the product path never imports this package).
 
-The far field of one matvec (Sec. 2.2-2.3, the regular-rule sum of Eqs. eqdbef3-eqdbef4 over
+The far field of one matvec (Sec. 2.2-2.3, the regular-rule sum of Eqs. (17)-(18) over
 every node of every element, written with sigma = sum_n W u_{N_v+v_n}/4pi, mu = sum_n W u_{v_n}/4pi
 and m = mu nu_y) is, for target vertex x with unit normal nu_x, d = x - y, r = |d|,
 E = exp(-kappa r), P = E (1 + kappa r), Q = E (3 + 3 kappa r + kappa^2 r^2):

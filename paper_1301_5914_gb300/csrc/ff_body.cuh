@@ -1,5 +1,5 @@
 // ff_body.cuh -- the far-field pair sum of one thread block, shared by the single-molecule
-// kernels (k_farfield.cu) and the batched persistent kernel (k_batch.cu) so both evaluate
+// kernels (k_farfield.cu) and the batched kernels (k_batch.cu) so both evaluate
 // exactly the same arithmetic. The formulas are documented in k_farfield.cu.
 #pragma once
 
@@ -237,7 +237,7 @@ __device__ __forceinline__ bool ff32_block(const float4* __restrict__ tgt, int n
 // FP32 rate, but its MUFU pipe returns 1/sqrt and 1/x seeds for doubles (rsqrt.approx.f64) at the
 // FP32 MUFU rate, and integer work runs beside both. So the FP64 far field takes 1/r from the MUFU
 // seed plus one Newton step, and exp(-kappa r) from a table plus a short polynomial, instead of the
-// library's full-range sqrt, division and exp: 45 FP64-pipe operations per pair instead of ~70.
+// library's full-range sqrt, division and exp: 44 FP64-pipe operations per pair instead of ~70.
 
 // 1/sqrt(x), x > 0 normal: seed y0 = rsqrt.approx.f64(x), then with e = 1 - x y0^2 (so that
 // x y0^2 = 1 - e), 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)). With the seed's
@@ -252,36 +252,37 @@ __device__ __forceinline__ double rsqrt_f64(double x) {
   return fma(y * e, p, y);
 }
 
-// 2^(j/64), j = 0..63, in shared memory: each far-field block fills it once (exp2 from the CUDA
-// math library; 64 evaluations per block).
-constexpr int kExpTable = 64;
+// 2^(j/256), j = 0..255, in shared memory: each FP64 far-field block fills it once (exp2 from the
+// CUDA math library; one evaluation per thread).
+constexpr int kExpTable = 256;
 __device__ __forceinline__ void exp_table_init(double* tab) {
   for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) tab[j] = exp2((double)j / kExpTable);
 }
 
-// 2^(t/64) for t <= 0 by Tang's table-driven method (ACM TOMS 15(2), 1989) with a 64-entry table:
-// t = n + f with n = round(t) (the 1.5 * 2^52 shift puts n in the low word) and |f| <= 1/2 exact,
-// 2^(t/64) = 2^floor(n/64) * 2^((n mod 64)/64) * exp(f ln2/64), the last factor by its Taylor
-// polynomial of degree 5 (|f ln2/64| <= 0.0055, truncation below 4e-17). The power of two is
-// added to the exponent field; n is clamped at -64 * 1021 (the result stays a normal double, at
-// most 2^-1020), so t below that (e^-707.7 and smaller: padding nodes, distant pairs) gives a
-// value within 5e-308 of the true one.
-// 3 + 5 + 1 FP64 operations; the rest is integer work.
-__device__ __forceinline__ double exp2_64th(double t, const double* __restrict__ tab) {
+// 2^(t/256) for -2^51 < t <= 0 by Tang's table-driven method (ACM TOMS 15(2), 1989) with a 256-entry
+// table: t = n + f with n = round(t) (the 1.5 * 2^52 shift puts n in the low word) and |f| <= 1/2
+// exact, 2^(t/256) = 2^floor(n/256) * 2^((n mod 256)/256) * exp(f ln2/256), the last factor by its
+// Taylor polynomial of degree 4 (|f ln2/256| <= 0.00136, truncation below 4e-17). The power of two
+// is added to the exponent field; n is clamped at -256 * 1021 (the result stays a normal double,
+// at most 2^-1020), so t below that (e^-707.7 and smaller: padding nodes, distant pairs) gives a
+// value within 5e-308 of the true one. 3 + 4 + 1 FP64 operations; the rest is integer work.
+__device__ __forceinline__ double exp2_256th(double t, const double* __restrict__ tab) {
   constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
-  constexpr double c = 0.693147180559945309417232121458 / 64.0;  // ln(2) / 64
-  constexpr double k2 = c * c / 2.0, k3 = k2 * c / 3.0, k4 = k3 * c / 4.0, k5 = k4 * c / 5.0;
+  constexpr double c = 0.693147180559945309417232121458 / kExpTable;  // ln(2) / 256
+  constexpr double k2 = c * c / 2.0, k3 = k2 * c / 3.0, k4 = k3 * c / 4.0;
   const double nd = t + kShift;
   const double f = t - (nd - kShift);
-  const int n = max(__double2loint(nd), -64 * 1021);
-  const double p = fma(fma(fma(fma(fma(k5, f, k4), f, k3), f, k2), f, c), f, 1.0);
+  // n = nd - kShift as integers (exact for |t| < 2^51), clamped before it is narrowed to 32 bits
+  const long long n64 = __double_as_longlong(nd) - __double_as_longlong(kShift);
+  const int n = (int)max(n64, (long long)(-kExpTable * 1021));
+  const double p = fma(fma(fma(fma(k4, f, k3), f, k2), f, c), f, 1.0);
   const double v = tab[n & (kExpTable - 1)] * p;
-  return __hiloint2double(__double2hiint(v) + (n >> 6) * (1 << 20), __double2loint(v));
+  return __hiloint2double(__double2hiint(v) + (n >> 8) * (1 << 20), __double2loint(v));
 }
 
 // Per-launch constants of the FP64 pair arithmetic (row 1 is summed divided by eps).
 struct FF64Consts {
-  double c64;         // -64 log2(e) (kappa-scaled tables) or -64 kappa log2(e): 2^(c64 r / 64) = E
+  double c256;        // -256 log2(e) (kappa-scaled tables) or -256 kappa log2(e): 2^(c256 r / 256) = E
   double kap, kap_sq; // unscaled mode: kappa, kappa^2
   double omie;        // 1 - 1/eps
   double row1_scale;  // eps xs
@@ -291,7 +292,7 @@ inline FF64Consts ff64_consts(double eps, double kappa) {
   const double xs = ff32_coord_scale(kappa);
   constexpr double kLog2e = 1.44269504088896340735992468100;
   FF64Consts c;
-  c.c64 = -64.0 * kLog2e * (ff32_kappa_scaled(kappa) ? 1.0 : kappa);
+  c.c256 = -kExpTable * kLog2e * (ff32_kappa_scaled(kappa) ? 1.0 : kappa);
   c.kap = kappa;
   c.kap_sq = kappa * kappa;
   c.omie = 1.0 - 1.0 / eps;
@@ -335,7 +336,7 @@ __device__ __forceinline__ void ff64_block(const double* __restrict__ tgt, int n
         double ir = rsqrt_f64(r2);
         if (SKIP_SELF) ir = r2 > 0.0 ? ir : 0.0;  // every term of a zero-distance pair then vanishes
         const double r = r2 * ir;
-        const double E = exp2_64th(r * cs.c64, tab);
+        const double E = exp2_256th(r * cs.c256, tab);
         const double Pm1 = fma(E, KS ? r + 1.0 : fma(cs.kap, r, 1.0), -1.0);  // P - 1
         const double aym = fma(dz, D.x, fma(dy, C.y, dx * C.x));             // d . m
         const double ir2 = ir * ir;
@@ -419,7 +420,7 @@ __device__ __forceinline__ void gather64_node(int node, int nv, const int* __res
 }
 
 // LOBI-PB node = face j: centroid y_j, face normal nu_j, weight A_j (area), densities from the
-// centroid unknowns u_j, u_{N_f+j} (Sec. 2.4, eqdbef1/eqdbef2).
+// centroid unknowns u_j, u_{N_f+j} (Sec. 2.4, Eqs. (21)/(22)).
 __device__ __forceinline__ void gather32_lobi(int j, int nf, const double* __restrict__ ny,
                                               const double* __restrict__ nnu, const double* __restrict__ nW,
                                               const double* __restrict__ center, const double* __restrict__ u,

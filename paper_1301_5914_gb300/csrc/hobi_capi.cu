@@ -1248,7 +1248,7 @@ int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double
   if (n == 0) return HOBI_OK;
   if (!x || !rsqrt_x || !exp_neg_x) return fail(HOBI_ERR_ARG, "NULL argument");
   for (int64_t k = 0; k < n; ++k)
-    if (!(x[k] >= 0.0 && x[k] < 1e300)) return fail(HOBI_ERR_ARG, "x must be finite and non-negative");
+    if (!(x[k] >= 0.0 && x[k] <= 1e12)) return fail(HOBI_ERR_ARG, "x must be in [0, 1e12]");
   double* d = nullptr;
   const size_t bytes = sizeof(double) * (size_t)n;
   if (cudaMalloc(&d, 3 * bytes) != cudaSuccess) return fail(HOBI_ERR_NOMEM, "cudaMalloc failed");
@@ -1278,13 +1278,14 @@ void hobi_destroy(hobi_t h) {
 // ---------------------------------------------------------------------------------------------
 // Reaction potential without any device allocation.
 //
-// For callers that cannot allocate device memory at call time: code that runs while a CUDA
-// stream is being captured into a graph (cudaMalloc is not allowed there), code that must not
-// trigger the device-wide synchronisation an allocation can cause, or hosts whose device memory
-// is owned by another allocator. The per-call scratch (the caller's points as targets, the
-// per-chunk partial sums and the reduced potentials) lives in one file-scope device array of
-// fixed size instead of buffers allocated on demand; the handle's own tables were allocated by
-// hobi_setup beforehand.
+// For callers that must not allocate device memory once they are running: a host whose device
+// memory is owned by another allocator (a framework's caching pool that holds the GPU's free
+// memory, so a cudaMalloc from this library would fail or break the pool's accounting), a
+// service whose memory footprint is fixed when it starts, and a latency-bound loop that cannot
+// pay cudaMalloc's cost and its synchronisation with the other streams of the device. The per-call
+// scratch (the caller's points as targets, the per-chunk partial sums and the reduced potentials)
+// lives in one file-scope device array of fixed size instead of buffers allocated on demand; the
+// handle's own tables were allocated by hobi_setup beforehand.
 namespace {
 
 constexpr int64_t kNoAllocMaxPoints = 4096;  // points per call
@@ -1324,6 +1325,7 @@ int noalloc_scratch(int dev, unsigned char** out) {
 }  // namespace
 
 extern "C" int hobi_reaction_potential_noalloc(hobi_t h, const double* points, int64_t n_points, double* phi) {
+  NvtxRange nvtx_range("hobi_reaction_potential_noalloc");
   if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
   if (n_points < 0 || (n_points > 0 && (!points || !phi))) return fail(HOBI_ERR_ARG, "bad points/phi arguments");
   if (n_points > kNoAllocMaxPoints)
@@ -1352,16 +1354,18 @@ extern "C" int hobi_reaction_potential_noalloc(hobi_t h, const double* points, i
   HOBI_TRY(h->copy_in(pts, points, 3 * n));
   HOBI_CK(launch_points((int)n, pts, 3, h->center, h->xs, t32, t64, h->stream));
   HOBI_TRY(h->gather(fp32, h->x, nullptr, 0));
-  HOBI_CK(launch_farfield(fp32, p, t32, t64, h->src32, h->src64, h->eps, h->kappa, part, h->ff_err, h->stream));
+  HOBI_TRY(h->farfield(fp32, p, t32, t64, part));  // timed like every far-field launch when profiling is on
   HOBI_CK(launch_reduce_points((int)n, p.chunks, part, phi_d, h->stream));
   h->launches += 4;
   HOBI_TRY(h->copy_out(phi, phi_d, n));
   HOBI_TRY(h->finish());
+  HOBI_TRY(h->collect_profile());
   return h->check_farfield();
 }
 
 // =============================================================================================
-// Batched solve: many molecules, one persistent far-field launch per GMRES step.
+// Batched solve: many molecules, one far-field launch per GMRES step (one block per task in FP32,
+// persistent blocks pulling tasks in FP64).
 // =============================================================================================
 struct hobi_batch_ctx {
   int device = 0;
@@ -1604,7 +1608,7 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
     if (r != HOBI_OK) return fail(r, "molecule " + std::to_string(m) + ": " + g_err);
     B->subs.push_back(h);
   }
-  // descriptors, partial-sum buffers and the persistent task lists
+  // descriptors, partial-sum buffers and the far-field task lists (one per precision)
   B->vert_off_h.assign(nmol + 1, 0);
   B->node_off_h.assign(nmol + 1, 0);
   std::vector<FFTask> tl[2];

@@ -1,5 +1,6 @@
-// k_batch.cu -- many molecules solved together: every GMRES step runs one persistent far-field
-// launch over a task list covering all unconverged molecules, plus batched gather, combine and
+// k_batch.cu -- many molecules solved together: every GMRES step runs one far-field launch over a
+// task list covering all unconverged molecules (FP32: one one-warp block per task; FP64: persistent
+// blocks pulling tasks from a counter), plus batched gather, combine and
 // FP64 Arnoldi/Givens kernels on the concatenation of the molecules' vectors.
 //
 // The per-pair arithmetic, the node densities and the combine step are the single-molecule

@@ -1,4 +1,4 @@
-// k_farfield.cu -- the per-iteration hot path of the HOBI-PB matvec (Sec. 2.2-2.3, Eqs. eqdbef3-6).
+// k_farfield.cu -- the per-iteration hot path of the HOBI-PB matvec (Sec. 2.2-2.3, Eqs. (17)-(20)).
 //
 // For every target vertex x_i (unit normal nu_i) and every regular-rule node y (normal nu_y) of
 // every element, the far-field kernel accumulates (d = x_i - y, r = |d|, E = exp(-kappa r),
@@ -8,7 +8,7 @@
 //   row 2:  nu_i . [ (P - 1)/r^3 m + ((P/eps - 1)/r^3 sigma - (Q - 3)/r^5 (d . m)) d ]
 //
 // with sigma = sum_n W_{j,m,n} u_{N_v + v_n} / (4 pi) and m = nu_y sum_n W_{j,m,n} u_{v_n} / (4 pi).
-// Row 1 is the K1/K2 sum of eqdbef3 and row 2 the K3/K4 sum of eqdbef4 (Eq_Ls written out), with
+// Row 1 is the K1/K2 sum of Eq. (17) and row 2 the K3/K4 sum of Eq. (18) (Eq. (10) written out), with
 // the target normal pulled out of the source sum so that each pair needs one vector
 // accumulation instead of two dot products. Faces incident to x_i are included here and
 // replaced by the singular rule through the precomputed correction (combine kernel).
@@ -128,9 +128,9 @@ __global__ void k_fp64_pair_functions(const double* __restrict__ x, int64_t n, d
   __syncthreads();
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  constexpr double kNegLog2e64 = -64.0 * 1.44269504088896340735992468100;
+  constexpr double kNegLog2eT = -ff::kExpTable * 1.44269504088896340735992468100;
   rs[k] = x[k] > 0.0 ? ff::rsqrt_f64(x[k]) : 1.0 / 0.0;
-  ex[k] = ff::exp2_64th(x[k] * kNegLog2e64, tab);
+  ex[k] = ff::exp2_256th(x[k] * kNegLog2eT, tab);
 }
 
 // ------------------------------------------------------------------ combine

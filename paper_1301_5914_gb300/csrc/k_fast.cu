@@ -2,7 +2,7 @@
 // paper, which evaluates the far field directly and names fast summation as future work; the
 // method is Wang, Tlupova and Krasny's kernel-independent treecode, 2020).
 //
-// The far-field sum of a matvec (the regular-rule part of Eqs. eqdbef3-eqdbef4) is linear in
+// The far-field sum of a matvec (the regular-rule part of Eqs. (17)-(18)) is linear in
 // the node densities sigma and m with coefficients that are smooth functions of the source
 // position away from the target. For a target batch B and a source cluster C that are well
 // separated, the sum over C's nodes is replaced by a sum over C's (n+1)^3 tensor Chebyshev

@@ -1,5 +1,5 @@
 // k_gmres.cu -- device-resident restarted GMRES in FP64 (the Krylov solver of the paper's
-// abstract and of the tb_MPI pseudocode, steps 11-17), written so that one iteration is a fixed
+// abstract and of the iteration loop in the Table 1 pseudocode), written so that one iteration is a fixed
 // sequence of kernels whose iteration index lives in device memory (GmresState.k): the host can
 // capture the sequence once as a CUDA graph and replay it.
 //

@@ -5,12 +5,12 @@
 //    exactly one opposite edge), referenced vertices, finite non-zero normals, positive volume
 //  * curved-element node generator (Sec. 2.2): cubic edge arcs through the vertices with the
 //    vertex normals, the 10 interpolation points, the cubic (10-point) interpolant
-//    (eqintepolation), and the 4 regular-rule nodes per element with position, unit normal and
-//    W_{j,m,n} = w_m J L_n (eqdbef3)
-//  * singular correction (Sec. 2.3, eqdbef5/eqdbef6): for each vertex i and each face j having i
+//    (Eq. (15)), and the 4 regular-rule nodes per element with position, unit normal and
+//    W_{j,m,n} = w_m J L_n (Eq. (17))
+//  * singular correction (Sec. 2.3, Eqs. (19)/(20)): for each vertex i and each face j having i
 //    as a corner, the 16-point Duffy/Gauss-Legendre sum minus the 4-point regular sum that the
 //    far-field kernel adds for the same face
-//  * right-hand side S1, S2 (Eq_Ss) with the charges' 1/eps1
+//  * right-hand side S1, S2 (Eq. (11)) with the charges' 1/eps1
 #include <math.h>
 
 #include "hobi_internal.cuh"
@@ -217,7 +217,7 @@ __device__ void arc_point(double3 P, double3 nP, double3 Q, double3 nQ, double t
 //   3,4  : arc X1->X2 at 1/3, 2/3      (1/3,0), (2/3,0)
 //   5,6  : arc X2->X3 at 1/3, 2/3      (2/3,1/3), (1/3,2/3)
 //   7,8  : arc X3->X1 at 1/3, 2/3      (0,2/3), (0,1/3)
-//   9    : (1/3,1/3) = (u,v) = (2/3,1/2) of eqrs2uv: arc Y1->Y2 at 1/2 with Y1 = arc X1->X2 at 2/3,
+//   9    : (1/3,1/3) = (u,v) = (2/3,1/2) of Eq. (14): arc Y1->Y2 at 1/2 with Y1 = arc X1->X2 at 2/3,
 //          Y2 = arc X1->X3 at 2/3 (= arc X3->X1 at 1/3 by the arc's symmetry)
 __device__ void element_points(double3 X1, double3 n1, double3 X2, double3 n2, double3 X3, double3 n3,
                                double3 p[10]) {
@@ -324,7 +324,7 @@ __global__ void k_node_gen(int nf, const int* F, const double* V, const double* 
   }
 }
 
-// ------------------------------------------------------------------ kernels K1..K4 (Eq_Ls)
+// ------------------------------------------------------------------ kernels K1..K4 (Eq. (10))
 // With d = x - y, r = |d|, E = exp(-kappa r), P = E (1 + kappa r), Q = E (3 + 3 kappa r + kappa^2 r^2):
 //   4 pi K1 = (1 - E)/r,  4 pi K2 = (eps P - 1) (d.ny)/r^3,  4 pi K3 = (P/eps - 1) (d.nx)/r^3,
 //   4 pi K4 = (P - 1)(nx.ny)/r^3 - (Q - 3)(d.nx)(d.ny)/r^5.
@@ -398,7 +398,7 @@ __global__ void k_correction(int n_entries, const int* vert, const int* F, const
     for (int q = 0; q < 4; ++q) corr[12 * (size_t)e + 4 * n + q] = acc[n][q];
 }
 
-// ------------------------------------------------------------------ right-hand side (Eq_Ss)
+// ------------------------------------------------------------------ right-hand side (Eq. (11))
 __global__ void k_rhs(int nv, int nc, const double* V, const double* Nv, const double* Q, double eps1,
                       double* b) {
   __shared__ double sq[256 * 4];

@@ -13,7 +13,7 @@ Workloads (sizes and seeds are the ones the tests and the benchmark use):
 * ``ball_charges(n, r_max, seed)``: n point charges uniform in a ball with
   values uniform in [-1, 1] e (the Kirkwood multi-charge sphere test).
 * ``synthetic_molecule(...)``: a globular "protein" stand-in for the paper's
-  1ajj workload (Sec. 3.3): seeded atoms, a Gaussian-density isosurface
+  1ajj workload (Sec. 3.4): seeded atoms, a Gaussian-density isosurface
   extracted by marching tetrahedra, analytic density-gradient normals.
 
 All arrays are float64 / int32, C-contiguous. Faces are counter-clockwise
@@ -469,7 +469,7 @@ def _surface(centers, radii, grid_h, pad=3.0, smooth_iters=6):
 def synthetic_molecule(n_atoms: int, seed: int, ball_radius: float | None = None, n_faces: int | None = None,
                        grid_h: float | None = None, centers=None, radii=None):
     """Seeded globular molecule and its Gaussian-density surface (stand-in for the paper's
-    MSMS surfaces of protein 1ajj, Sec. 3.3).
+    MSMS surfaces of protein 1ajj, Sec. 3.4).
 
     Atoms: sequential random packing in a ball (radius 20 A * (n_atoms/1000)**(1/3) by
     default), radii U[1.2, 2.0] A; charges N(0, 0.4) e shifted so the net charge is an integer.

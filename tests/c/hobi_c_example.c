@@ -1,7 +1,7 @@
 /* A C program using the library through include/hobi.h only: plain host pointers, no Python.
  * Builds a sphere (octahedron refined `level` times, vertices projected to radius R, exact radial
  * normals), puts a +1 e charge at the centre, solves in both precisions and prints the
- * solvation energy next to the Born value -C/2 (1/eps1 - 1/eps2) q^2 / R (Sec. 3.1, Table 1).
+ * solvation energy next to the Born value -C/2 (1/eps1 - 1/eps2) q^2 / R (Sec. 3.2, Table 2).
  * Usage: hobi_c_example [level] [radius]; exit status 0 when both solves converge. */
 #include <math.h>
 #include <stdio.h>

@@ -1,6 +1,6 @@
 """The C ABI used from C: tests/c/hobi_c_example.c includes only include/hobi.h and links
 libhobi.so. On the CPU it must compile and link; on the GPU its FP64 and FP32 solves of a
-refined-octahedron sphere must reproduce the Born energy (Sec. 3.1, Table 1)."""
+refined-octahedron sphere must reproduce the Born energy (Sec. 3.2, Table 2)."""
 import os
 import re
 import subprocess

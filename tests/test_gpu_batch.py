@@ -1,4 +1,4 @@
-"""Batched solve (one persistent far-field launch per GMRES step for all molecules) against the
+"""Batched solve (one far-field launch per GMRES step for all molecules) against the
 single-molecule path and the oracle: every molecule's result must equal its own solve."""
 import numpy as np
 import pytest
@@ -39,7 +39,7 @@ def _rel(a, b):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
 def test_batch_matches_single_solves(molecules, prec, tol):
     """FP64: same arithmetic up to the order of FP64 chunk sums. FP32: the batch uses the
-    256-node tile shape in 16-tile tasks while a single solve may use another autotuned shape
+    128-node tile shape in 32-tile tasks while a single solve may use another autotuned shape
     (other FP32 tile sums) -- differences far below the FP32-bulk tolerance (1e-4)."""
     bs = hobi.BatchSolver(molecules, EPS1, EPS2, KAPPA, precision=prec)
     phis, dphis, info = bs.solve(1e-6, 200)

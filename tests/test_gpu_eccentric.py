@@ -1,6 +1,6 @@
-"""Eccentric-charge sphere study of Sec. 3.2 (Fig. 3c-f), regenerated on icospheres: radius 1 A,
+"""Eccentric-charge sphere study of Sec. 3.3 (Fig. 4c-f), regenerated on icospheres: radius 1 A,
 one +1 e charge moved from the centre toward the surface, kappa = 1, eps = 80, HOBI-PB and
-LOBI-PB against the Kirkwood series, surface-potential error e_phi (Eq. eqerr1) per
+LOBI-PB against the Kirkwood series, surface-potential error e_phi (Eq. (24)) per
 icosahedral level. The figure's data are not in the paper; the test checks the paper's
 observations that hold on uniform meshes, and writes the table as JSON into the directory named
 by the environment variable HOBI_STUDY_OUT when it is set."""
@@ -56,7 +56,7 @@ def table():
 
 
 def test_hobi_more_accurate_for_interior_charges(table):
-    """Observation (1) of Sec. 3.2: HOBI errors are smaller than LOBI's."""
+    """Observation (1) of Sec. 3.3: HOBI errors are smaller than LOBI's."""
     for L in LEVELS[1:]:
         for x in (0.0, 0.3, 0.5):
             assert table[("hobi", L, x)][0] < table[("lobi", L, x)][0], (L, x)
@@ -64,13 +64,13 @@ def test_hobi_more_accurate_for_interior_charges(table):
 
 def _slope(table, scheme, x, levels=(2, 3, 4, 5)):
     """Least-squares order in the density d (x4 per level); HOBI's pattern is irregular near the
-    surface (Sec. 3.2, observation (2)), so two-level ratios can mislead."""
+    surface (Sec. 3.3, observation (2)), so two-level ratios can mislead."""
     e = np.log([table[(scheme, L, x)][0] for L in levels])
     return -np.polyfit(np.log(4.0) * np.array(levels), e, 1)[0]
 
 
 def test_hobi_converges_faster(table):
-    """Fig. 3e/f: a steeper error-vs-elements slope for HOBI than for LOBI; LOBI near half order."""
+    """Fig. 4e/f: a steeper error-vs-elements slope for HOBI than for LOBI; LOBI near half order."""
     for x in (0.0, 0.5, 0.9):
         sh, sl = _slope(table, "hobi", x), _slope(table, "lobi", x)
         assert sh > sl > 0.2, (x, sh, sl)
@@ -81,6 +81,6 @@ def test_errors_fall_with_refinement_and_grow_near_surface(table):
     for scheme in ("hobi", "lobi"):
         for x in POSITIONS:
             assert table[(scheme, 5, x)][0] < table[(scheme, 2, x)][0]
-        # a charge close to the interface is harder (Sec. 3.2): at every level
+        # a charge close to the interface is harder (Sec. 3.3): at every level
         for L in LEVELS:
             assert table[(scheme, L, 0.9)][0] > table[(scheme, L, 0.0)][0]

@@ -2,7 +2,7 @@
 
 For kappa at or above 1e-6 1/A the FP32 tables hold coordinates multiplied by kappa (the pair
 formula then needs no kappa r product); below it, kappa = 0 included, they are unscaled. Both
-modes must give the same operator (Eqs. eqdbef3-eqdbef4), reaction potential and energy
+modes must give the same operator (Eqs. (17)-(18)), reaction potential and energy
 (Sec. 2.5) as the oracle, on either side of the switch, for single molecules and batches.
 """
 import numpy as np

@@ -1,4 +1,4 @@
-"""LOBI-PB (Sec. 2.4, eqdbef1/eqdbef2) on the GPU against the oracle's LOBI scheme: flat-face
+"""LOBI-PB (Sec. 2.4, Eqs. (21)/(22)) on the GPU against the oracle's LOBI scheme: flat-face
 geometry, right-hand side, matvec (self pair skipped), GMRES and energy, both precisions."""
 import numpy as np
 import pytest

@@ -9,6 +9,7 @@ import pytest
 import oracle
 from oracle import kirkwood as kw
 from paper_1301_5914_gb300 import hobi, synth
+from rowsample import boundary_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +62,8 @@ def test_molecule_matvec_sampled_rows(molecule):
     s = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp64")
     rng = np.random.default_rng(4)
     u = rng.normal(size=2 * s.nv)
-    rows = np.concatenate([_rows(s.nv, 40, 1), [0, s.nv - 1]])
+    rows = boundary_rows(s.nv, 64, 1)
+    assert rows.size >= 300
     _check_rows(s.matvec(u), orc, u, rows, 1e-10)
     # FP32 bulk on a smooth density (the FP64 solution) and on the random vector
     phi, dphi, info = s.solve(1e-6, 200)
@@ -107,7 +109,8 @@ def test_bench_workload_full_size_fp32():
     phi, dphi, info = s.solve(1e-6, 200)
     assert info["converged"]
     u = np.concatenate([phi, dphi])
-    rows = np.concatenate([_rows(s.nv, 24, 2), [0, s.nv - 1]])
+    rows = boundary_rows(s.nv, 128, 2)
+    assert rows.size >= 512
     _check_rows(s.matvec(u), orc, u, rows, 2e-5)
     E = s.energy()
     e_ex = kw.solvation_energy(Q, 10.0, 1.0, 80.0, 0.1257)

@@ -185,7 +185,7 @@ def test_energy_and_reaction_potential_given_solution(problems):
 
 
 def test_born_sphere_on_gpu():
-    """Table 1 on the GPU: E_sol = -81.98 for the radius-2 sphere, both precisions."""
+    """Table 2 on the GPU: E_sol = -81.98 for the radius-2 sphere, both precisions."""
     V, F, N = synth.icosphere(3, 2.0)
     for prec in ("fp64", "fp32"):
         s = hobi.Solver(V, F, N, synth.point_charge(0, 0, 0, 1.0), 1.0, 80.0, 0.0, precision=prec)

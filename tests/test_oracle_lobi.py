@@ -1,4 +1,4 @@
-"""Pins of the oracle's low-order LOBI-PB scheme (Sec. 2.4, eqdbef1/eqdbef2): flat triangles,
+"""Pins of the oracle's low-order LOBI-PB scheme (Sec. 2.4, Eqs. (21)/(22)): flat triangles,
 centroid collocation, self triangle dropped."""
 import numpy as np
 
@@ -30,7 +30,7 @@ def test_lobi_geometry_is_flat_faces():
 
 
 def test_lobi_born_half_order_and_table1_band():
-    """Table 1 (LOBI-PB column): surface-potential error converges at about half order in the
+    """Table 2 (LOBI-PB column): surface-potential error converges at about half order in the
     density d, and E_sol approaches -81.98 from below (-83.41 at d = 5 ... -82.43 at d = 80)."""
     out = [_born(L) for L in (2, 3, 4)]
     e = [o[2] for o in out]
@@ -38,7 +38,7 @@ def test_lobi_born_half_order_and_table1_band():
     orders = [np.log(e[k] / e[k + 1]) / np.log(4.0) for k in range(2)]
     assert all(0.35 < o < 0.8 for o in orders), orders
     assert E[0] < E[1] < E[2] < -81.98
-    assert abs(E[2] - (-82.60)) < 0.3  # level 4 (d = 51) vs Table 1 at d = 40
+    assert abs(E[2] - (-82.60)) < 0.3  # level 4 (d = 51) vs Table 2 at d = 40
 
 
 def test_lobi_double_layer_identity_kappa0():
@@ -92,7 +92,7 @@ def test_lobi_screened_eccentric_charge_vs_kirkwood():
 
 
 def test_lobi_matvec_is_the_centroid_rule_written_out():
-    """Eqs. eqdbef1/eqdbef2 with the centroid rule, written out here with numpy geometry and the
+    """Eqs. (21)/(22) with the centroid rule, written out here with numpy geometry and the
     oracle's kernels K1-K4 (pinned to finite differences of G0, G_kappa):
     (Au)_i = 1/2 (1 + eps) u_i - sum_{j != i} A_j [K1 u_nu,j + K2 u_j], and row 2 with
     1/2 (1 + 1/eps) and K3, K4."""
@@ -120,7 +120,7 @@ def test_lobi_matvec_is_the_centroid_rule_written_out():
 
 
 def test_lobi_rhs_is_the_source_terms_at_the_centroids():
-    """Eq. Eq_Ss with the charge potential q/(4 pi eps1 r) of region 1, at the centroids and with
+    """Eq. (11) with the charge potential q/(4 pi eps1 r) of region 1, at the centroids and with
     the flat face normals (eps1 = 2, so a dropped 1/eps1 shows)."""
     V, F, N = synth.icosphere(2, 2.0)
     Q = synth.ball_charges(3, 1.2, 9)
@@ -139,7 +139,7 @@ def test_lobi_rhs_is_the_source_terms_at_the_centroids():
 
 def test_lobi_born_with_eps1_2():
     """Born ion with eps1 = 2: E_sol = -C q^2 (1/eps1 - 1/eps2) / (2a) = -40.47 kcal/mol, approached
-    from below as in Table 1's LOBI column (measured 5.3 % then 2.0 % high in magnitude)."""
+    from below as in Table 2's LOBI column (measured 5.3 % then 2.0 % high in magnitude)."""
     ex = -0.5 * kw.C_KCAL * (1 / 2.0 - 1 / 80.0) / 2.0
     E = []
     for L in (2, 3):

@@ -63,7 +63,7 @@ NODES_RS = [(0, 0), (1, 0), (0, 1), (1 / 3, 0), (2 / 3, 0), (0, 1 / 3), (0, 2 / 
 
 
 def test_p3_basis_kronecker_and_unity():
-    """10-point cubic interpolant (eqintepolation): N_k(node_l) = delta_kl, sum N = 1."""
+    """10-point cubic interpolant (Eq. (15)): N_k(node_l) = delta_kl, sum N = 1."""
     for l, (r, s) in enumerate(NODES_RS):
         N, _, _ = oracle.p3_basis(r, s)
         e = np.zeros(10)
@@ -146,7 +146,7 @@ def _G(x, y, kappa):
 
 @pytest.mark.parametrize("kappa", [0.0, 0.1257, 1.0])
 def test_kernels_match_finite_differences(kappa):
-    """K1..K4 (Eq_Ls) against central differences of G0 and Gk (eq_potential)."""
+    """K1..K4 (Eq. (10)) against central differences of G0 and Gk (eq_potential)."""
     rng = np.random.default_rng(1)
     eps = 80.0
     for _ in range(6):
@@ -226,7 +226,7 @@ def test_kirkwood_limits():
     for kappa in (0.0, 0.1257, 1.0):
         Ek = kw.solvation_energy(np.array([[0, 0, 0, 1.0]]), 2.0, 1.0, 80.0, kappa)
         assert abs(Ek - kw.born_energy(1.0, 2.0, 1.0, 80.0, kappa)) < 1e-12
-    assert abs(kw.born_energy(1.0, 2.0, 1.0, 80.0) - (-81.98)) < 0.005  # Table 1 exact value
+    assert abs(kw.born_energy(1.0, 2.0, 1.0, 80.0) - (-81.98)) < 0.005  # Table 2 exact value
     B0 = kw.reaction_coeffs(20, 3.0, 2.0, 80.0, 0.0)
     B1 = kw.reaction_coeffs(20, 3.0, 2.0, 80.0, 1e-9)
     n = np.arange(21)
@@ -245,23 +245,24 @@ def born_l3():
     return p, u, it, conv
 
 
-def _golden_table1():
+def _golden(name, ncol):
     rows = []
-    with open(__file__.replace("test_oracle_pins.py", "golden/table1_hobi_sphere.txt")) as f:
+    with open(__file__.replace("test_oracle_pins.py", "golden/" + name)) as f:
         for line in f:
             if line.strip() and not line.startswith("#"):
-                d, e, ephi = line.split()
-                rows.append((float(d), float(e), float(ephi)))
+                vals = line.split()
+                assert len(vals) == ncol
+                rows.append(tuple(float(v) for v in vals))
     return rows
 
 
-def test_born_sphere_matches_table1(born_l3):
-    """Table 1: E_sol = -81.98 kcal/mol for the radius-2 sphere (printed to 2 decimals);
+def test_born_sphere_matches_table2(born_l3):
+    """Table 2: E_sol = -81.98 kcal/mol for the radius-2 sphere (printed to 2 decimals);
     e_phi at density ~12.8 lies within the paper's band for d = 5..20."""
     p, u, it, conv = born_l3
     assert conv
     E = p.energy(u)
-    gold = _golden_table1()
+    gold = _golden("table2_hobi_sphere.txt", 3)
     assert round(E, 2) == gold[0][1]
     phi_ex, dphi_ex = kw.surface_potential(p.V, p.charges, 2.0, 1.0, 80.0, 0.0)
     ephi = np.max(np.abs(u[: p.nv] - phi_ex)) / np.max(np.abs(phi_ex))
@@ -321,12 +322,18 @@ def test_eccentric_charge_kirkwood_c1():
     """Radius-2 sphere, +1 e at (0.5,0,0), eps1=1, eps2=80, kappa=0.1257, icosphere L3:
     surface potential and E_sol against the Kirkwood series; error falls under refinement."""
     Q = synth.point_charge(0.5, 0, 0, 1.0)
+    # Table 3 prints 9-13 GMRES iterations for protein 1ajj at every density; the iteration count
+    # of a second-kind system depends little on the mesh, but a sphere is not that protein, so the
+    # band is a ballpark (widened by 1 below and 3 above), not a parity value.
+    its = [row[2] for row in _golden("table3_1ajj_iterations.txt", 3)]
+    lo, hi = min(its), max(its)
+    assert (lo, hi) == (9, 13)
     out = []
     for L in (2, 3):
         V, F, N = synth.icosphere(L, 2.0)
         p = oracle.Problem(V, F, N, Q, 1.0, 80.0, 0.1257)
         u, it, conv, _ = p.gmres(1e-6)
-        assert conv and 8 <= it <= 16  # the paper's GMRES counts are 9-13 (Table 2)
+        assert conv and lo - 1 <= it <= hi + 3, (it, lo, hi)
         phi_ex, dphi_ex = kw.surface_potential(V, Q, 2.0, 1.0, 80.0, 0.1257)
         ephi = np.max(np.abs(u[: p.nv] - phi_ex)) / np.max(np.abs(phi_ex))
         Eex = kw.solvation_energy(Q, 2.0, 1.0, 80.0, 0.1257)

@@ -81,7 +81,7 @@ def test_direct_far_is_the_regular_rule_kernel_sum():
     """The module's pair formula and node densities against the oracle's kernels K1-K4 (pinned
     to finite differences of G0 and G_kappa) summed node by node with the regular-rule weights
     W_{j,m,n}; and the oracle's matvec rows rebuilt from that sum, the diagonal and the 16-point
-    rule on the incident faces (Eqs. eqdbef3-eqdbef6)."""
+    rule on the incident faces (Eqs. (17)-(20))."""
     V, F, N = synth.icosphere(1, 2.0)
     orc = oracle.Problem(V, F, N, synth.ball_charges(2, 1.2, 5), 1.0, 80.0, 0.3)
     u = np.random.default_rng(4).normal(size=2 * orc.nv)
