@@ -490,7 +490,7 @@ def lobi_object(hobi, arrays, e1, e2, ka, tol, stream, sms, fmax):
     s.close()
     return {"scheme": "LOBI-PB (flat faces, centroid collocation, self term dropped)", "n_unknowns": 2 * s.npts,
             "pairs_per_matvec": pairs, "farfield_ms": launch_s * 1e3, "pairs_per_s": pairs / launch_s,
-            "frac_fp32_lane_peak": frac, "ops_per_pair": f"{OPS_PER_PAIR} FP32 FMA-pipe + zero-distance select",
+            "frac_fp32_lane_peak": frac, "ops_per_pair": f"{OPS_PER_PAIR} FP32 FMA-pipe (+ a zero-distance select in the tiles holding the block's own targets)",
             "gmres_fp32_bulk_s": info["solve_ms"] / 1e3, "iterations": info["iterations"], "E_sol": E}
 
 

@@ -3,6 +3,8 @@
 // exactly the same arithmetic. The formulas are documented in k_farfield.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "hobi_internal.cuh"
 
 namespace hobi {
@@ -80,18 +82,22 @@ struct ContigTiles {
   int t0;
   __device__ __forceinline__ const float4* ptr(int k) const { return src + (size_t)(t0 + k) * (4 * TILE); }
   __device__ __forceinline__ int count(int) const { return TILE; }
+  __device__ __forceinline__ int first_node(int k) const { return (t0 + k) * TILE; }
 };
 struct SegmentTiles {
   const float4* src;
   const int2* seg;
   __device__ __forceinline__ const float4* ptr(int k) const { return src + 4 * (size_t)seg[k].x; }
   __device__ __forceinline__ int count(int k) const { return seg[k].y; }
+  __device__ __forceinline__ int first_node(int k) const { return seg[k].x; }
 };
 
 // One block's FP32 far field: NT threads with 2 TP targets each (targets first + threadIdx.x +
 // k NT, below lim) against `ntile` source tiles of at most TILE nodes; results (FP64) to
 // out[o] (row 1) and out[ld2 + o] (row 2), o = map[i] (or i without a map). SKIP_SELF: a pair at
-// zero distance (a collocation point that is also a source node, LOBI-PB) contributes nothing.
+// zero distance (a collocation point that is also a source node, LOBI-PB, where target i is
+// source node i) contributes nothing; only the tiles that hold some of the block's own targets
+// run the pair body with the zero-distance test, the others the plain body.
 // KS: coordinates and m are stored multiplied by kappa (FF32Consts), so kappa r is the scaled
 // distance itself.
 // Tiles stream through two shared-memory stages (sh: 2 x 4 TILE float4) by bulk asynchronous
@@ -147,6 +153,9 @@ __device__ __forceinline__ bool ff32_core(const float4* __restrict__ tgt, int fi
     float2 a1[TP], wx[TP], wy[TP], wz[TP];
 #pragma unroll
     for (int k = 0; k < TP; ++k) a1[k] = wx[k] = wy[k] = wz[k] = pair_of(0.f);
+    // the tile's pair sums; SELF: with the zero-distance test (a uniform choice per tile)
+    auto tile_sum = [&](auto self_tag) {
+      constexpr bool SELF = decltype(self_tag)::value;
 #pragma unroll kUnroll
     for (int s = 0; s < cnt; ++s) {
       const float4 A = cur[4 * s], B = cur[4 * s + 1], C = cur[4 * s + 2], D = cur[4 * s + 3];
@@ -158,7 +167,7 @@ __device__ __forceinline__ bool ff32_core(const float4* __restrict__ tgt, int fi
         const float2 dx = __fadd2_rn(px[k], nyx), dy = __fadd2_rn(py[k], nyy), dz = __fadd2_rn(pz[k], nyz);
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-        if (SKIP_SELF) {  // 1/r -> 0 before anything else: every term of the pair then vanishes
+        if (SELF) {  // 1/r -> 0 before anything else: every term of the pair then vanishes
           ir.x = r2.x > 0.f ? ir.x : 0.f;
           ir.y = r2.y > 0.f ? ir.y : 0.f;
         }
@@ -193,6 +202,16 @@ __device__ __forceinline__ bool ff32_core(const float4* __restrict__ tgt, int fi
           wz[k] = __ffma2_rn(w, mz, __ffma2_rn(sv, dz, wz[k]));
         }
       }
+    }
+    };
+    if constexpr (SKIP_SELF) {
+      const int n0 = tiles.first_node(kt);
+      if (n0 < first + NT * T && n0 + cnt > first)
+        tile_sum(std::true_type{});
+      else
+        tile_sum(std::false_type{});
+    } else {
+      tile_sum(std::false_type{});
     }
 #pragma unroll
     for (int k = 0; k < TP; ++k) {
