@@ -270,6 +270,17 @@ int hobi_fast_plan_stats(const double* nodes, int64_t n_nodes, const double* tar
  * are HOST arrays. Allocates and frees temporary device memory. */
 int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x);
 
+/* Failure-path check of the far-field source-tile pipeline (no counterpart in the paper). The
+ * far-field kernels wait for each bulk-copied source tile on a shared-memory barrier, and every
+ * wait is bounded: after about a second without the copy's arrival the kernel sets the handle's
+ * error flag, drains its own copies and returns, and the call that launched it returns
+ * HOBI_ERR_CUDA ("far-field source-tile pipeline timed out"). This call exercises that path
+ * without faulting anything: one warp, on the handle's stream, initialises the tile barriers as
+ * the kernels do and waits on a phase that no copy will complete. Expected result: HOBI_ERR_CUDA
+ * with that message after about one second (*elapsed_ms, nullable host pointer, receives the
+ * kernel's duration); the flag is then cleared and the handle stays usable. */
+int hobi_check_tile_wait_timeout(hobi_t h, double* elapsed_ms);
+
 /* Free every resource of the handle (NULL is a no-op). */
 void hobi_destroy(hobi_t h);
 

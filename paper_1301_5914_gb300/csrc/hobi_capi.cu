@@ -805,6 +805,25 @@ int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double
   return HOBI_OK;
 }
 
+int hobi_check_tile_wait_timeout(hobi_t h, double* elapsed_ms) {
+  NvtxRange nvtx_range("hobi_check_tile_wait_timeout");
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  HOBI_CK(cudaEventRecord(h->ev_t0, h->stream));
+  HOBI_CK(launch_tile_wait_check(h->ff_err, h->stream));
+  HOBI_CK(cudaEventRecord(h->ev_t1, h->stream));
+  h->launches += 1;
+  HOBI_TRY(h->leave());
+  HOBI_CK(cudaEventSynchronize(h->ev_t1));
+  if (elapsed_ms) {
+    float ms = 0.f;
+    HOBI_CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+    *elapsed_ms = ms;
+  }
+  return h->check_farfield();
+}
+
 int hobi_kernel_launches(hobi_t h, int64_t* n) {
   if (!h || !n) return fail(HOBI_ERR_ARG, "NULL argument");
   *n = h->launches;

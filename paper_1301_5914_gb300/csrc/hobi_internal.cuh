@@ -141,6 +141,9 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
 // The FP64 far field's own 1/sqrt(x) and exp(-x) on n points (device arrays).
 cudaError_t launch_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x,
                                        cudaStream_t s);
+// One warp waits, with the far-field kernels' bounded wait, on a tile barrier nothing completes,
+// and sets *err when the wait gives up (failure-path check).
+cudaError_t launch_tile_wait_check(int* err, cudaStream_t s);
 // LOBI-PB node densities (one node per face)
 cudaError_t launch_gather_lobi(bool fp32, int nf, const double* ny, const double* nnu, const double* nW,
                                const double* center, const double* u, const int* kptr, int64_t ld, double inv_eps,

@@ -133,6 +133,18 @@ __global__ void k_fp64_pair_functions(const double* __restrict__ x, int64_t n, d
   ex[k] = ff::exp2_256th(x[k] * kNegLog2eT, tab);
 }
 
+// Failure-path check of the source-tile pipeline: one warp initialises the two tile barriers
+// exactly as the far-field kernels do and waits, through the same bounded wait, on a phase that no
+// copy will complete. The wait gives up after its spin bound and the kernel sets *err like a far-
+// field block whose bulk copy never arrived (no copy is in flight, so nothing is left to drain).
+__global__ void k_tile_wait_check(int* err) {
+  __shared__ __align__(8) unsigned long long bars[2];
+  if (threadIdx.x == 0) ff::tile_barriers_init(bars);
+  __syncthreads();
+  const bool ok = ff::tile_wait(&bars[0], 0u);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, 1);
+}
+
 // ------------------------------------------------------------------ combine
 // Au_i = (1/2)(1+eps) u_i - [sum_c part_c,i + sum over incident entries of corr . (u_{N_v+v}, u_v)]
 // Au_{N_v+i} = (1/2)(1+1/eps) u_{N_v+i} - [...] with the K3/K4 coefficients. Diagonal once.
@@ -327,6 +339,11 @@ cudaError_t launch_farfield(bool fp32, const FarFieldPlan& p, const float4* tgt3
 cudaError_t launch_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x,
                                        cudaStream_t s) {
   if (n > 0) k_fp64_pair_functions<<<nblk(n, 256), 256, 0, s>>>(x, n, rsqrt_x, exp_neg_x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_wait_check(int* err, cudaStream_t s) {
+  k_tile_wait_check<<<1, 32, 0, s>>>(err);
   return cudaGetLastError();
 }
 

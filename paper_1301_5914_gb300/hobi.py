@@ -37,7 +37,7 @@ EXPORTS = [
     "hobi_solve", "hobi_solve_from", "hobi_solve_refined", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
     "hobi_reaction_potential_noalloc", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
-    "hobi_fast_info", "hobi_fast_plan_stats", "hobi_fp64_pair_functions",
+    "hobi_fast_info", "hobi_fast_plan_stats", "hobi_fp64_pair_functions", "hobi_check_tile_wait_timeout",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
     "hobi_matvec_batch", "hobi_solve_batch", "hobi_energy_batch", "hobi_batch_kernel_launches", "hobi_destroy_batch",
     "hobi_batch_profile_enable", "hobi_batch_profile_read",
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_fast_plan_stats.argtypes = [dp, i64, dp, i64, C.c_int32, C.c_double, C.POINTER(i64), C.POINTER(i64),
                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.hobi_fp64_pair_functions.argtypes = [dp, i64, dp, dp]
+    lib.hobi_check_tile_wait_timeout.argtypes = [vp, C.POINTER(C.c_double)]
     lib.hobi_destroy.argtypes = [vp]
     lib.hobi_destroy.restype = None
     lib.hobi_setup_batch.argtypes = [C.c_int32, dp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
@@ -427,6 +428,13 @@ class Solver:
         _check(self._lib.hobi_fast_info(self._h, C.byref(d), C.byref(a), C.byref(b), C.byref(p), C.byref(t)))
         return {"direct_pairs": d.value, "approx_pairs": a.value, "batches": b.value, "proxy_clusters": p.value,
                 "tasks": t.value}
+
+    def check_tile_wait_timeout(self):
+        """Run the far-field tile pipeline's bounded wait on a barrier nothing completes: returns
+        (status code, message, kernel milliseconds); the expected status is HOBI_ERR_CUDA."""
+        ms = C.c_double()
+        code = self._lib.hobi_check_tile_wait_timeout(self._h, C.byref(ms))
+        return code, self._lib.hobi_last_error().decode() if code != HOBI_OK else "", ms.value
 
     def profile_enable(self, on: bool = True):
         _check(self._lib.hobi_profile_enable(self._h, 1 if on else 0))
