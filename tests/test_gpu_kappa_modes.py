@@ -1,9 +1,10 @@
-"""FP32 far field in both of its coordinate modes against the FP64 oracle.
+"""FP32 and FP64 far fields in both of their coordinate modes against the FP64 oracle.
 
-For kappa at or above 1e-6 1/A the FP32 tables hold coordinates multiplied by kappa (the pair
-formula then needs no kappa r product); below it, kappa = 0 included, they are unscaled. Both
-modes must give the same operator (Eqs. (17)-(18)), reaction potential and energy
-(Sec. 2.5) as the oracle, on either side of the switch, for single molecules and batches.
+For kappa at or above 1e-6 1/A the far-field tables (FP32 and FP64 alike) hold coordinates
+multiplied by kappa (the pair formula then needs no kappa r product); below it, kappa = 0
+included, they are unscaled. Both modes must give the same operator (Eqs. (17)-(18)), reaction
+potential and energy (Sec. 2.5) as the oracle, on either side of the switch, for single
+molecules, LOBI-PB and batches: FP32 within its bulk tolerances, FP64 within 1e-10.
 """
 import numpy as np
 import pytest
@@ -80,4 +81,48 @@ def test_batch_fp32_both_modes(kappa):
         n = 2 * m[0].shape[0]
         orc = oracle.Problem(*m, 1.0, 80.0, kappa)
         assert _rel(Au[off:off + n], orc.matvec(u[off:off + n])) <= 1e-5
+        off += n
+
+
+@pytest.mark.parametrize("kappa", KAPPAS)
+def test_fp64_matvec_energy_and_potential_both_modes(sphere, kappa):
+    V, F, N, Q = sphere
+    orc = oracle.Problem(V, F, N, Q, 1.0, 80.0, kappa)
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, kappa, precision="fp64")
+    u = np.random.default_rng(23).normal(size=2 * s.nv)
+    ref = orc.matvec(u)
+    assert np.max(np.abs(s.matvec(u) - ref)) <= 1e-10 * np.max(np.abs(ref))
+    u_sol, _, _, _ = orc.gmres(1e-8)
+    s.set_solution(u_sol)
+    e_ref = orc.energy(u_sol)
+    assert abs(s.energy() - e_ref) <= 1e-10 * abs(e_ref)
+    pts = np.array([[0.3, -0.2, 0.1], [1.0, 1.5, -0.5], [0.0, 0.0, 2.5]])
+    ref_p = orc.reaction_potential(u_sol, pts)
+    assert np.max(np.abs(s.reaction_potential(pts) - ref_p)) <= 1e-10 * np.max(np.abs(ref_p))
+
+
+@pytest.mark.parametrize("kappa", [0.0, 5e-7, 0.1257])
+def test_lobi_fp64_both_modes(sphere, kappa):
+    V, F, N, Q = sphere
+    orc = oracle.LobiProblem(V, F, N, Q, 1.0, 80.0, kappa)
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, kappa, precision="fp64", scheme="lobi")
+    u = np.random.default_rng(24).normal(size=2 * s.npts)
+    ref = orc.matvec(u)
+    assert np.max(np.abs(s.matvec(u) - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("kappa", [0.0, 5e-7, 0.1257])
+def test_batch_fp64_both_modes(kappa):
+    mols = []
+    for k, (lvl, rad) in enumerate([(2, 3.0), (3, 5.0), (1, 2.0)]):
+        V, F, N = synth.icosphere(lvl, rad)
+        mols.append((V, F, N, synth.ball_charges(3, 0.6 * rad, 50 + k)))
+    b = hobi.BatchSolver(mols, 1.0, 80.0, kappa, precision="fp64")
+    u = np.random.default_rng(41).normal(size=2 * b.nv_total)
+    Au = b.matvec(u)
+    off = 0
+    for m in mols:
+        n = 2 * m[0].shape[0]
+        ref = oracle.Problem(*m, 1.0, 80.0, kappa).matvec(u[off:off + n])
+        assert np.max(np.abs(Au[off:off + n] - ref)) <= 1e-10 * np.max(np.abs(ref))
         off += n
