@@ -281,7 +281,10 @@ int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double
  * kernel's duration); the flag is then cleared and the handle stays usable. */
 int hobi_check_tile_wait_timeout(hobi_t h, double* elapsed_ms);
 
-/* Free every resource of the handle (NULL is a no-op). */
+/* Free every resource of the handle (NULL is a no-op). Its device memory goes back to the
+ * library's stream-ordered memory pool for that device, which keeps it for the next handle
+ * (setting up a handle then costs no cudaMalloc, destroying one no device-wide cudaFree) and
+ * holds it until the process exits. */
 void hobi_destroy(hobi_t h);
 
 /* ---------------------------------------------------------------------------------------

@@ -7,6 +7,64 @@
 namespace hobi {
 namespace host {
 thread_local std::string g_err;
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+std::mutex g_pinned_mu;
+std::vector<void*> g_pinned_free;
+}  // namespace
+
+cudaError_t pool_alloc(void** p, size_t bytes, int device, cudaStream_t s) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[device]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      cudaMemPool_t created = nullptr;
+      cudaError_t e = cudaMemPoolCreate(&created, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;  // hold freed memory for the next handle
+      e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(created);
+        return e;
+      }
+      g_pool[device] = created;
+    }
+    pool = g_pool[device];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t pool_free(void* p, cudaStream_t s) { return cudaFreeAsync(p, s); }
+
+void* pinned_slot() {
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  if (g_pinned_free.empty()) {
+    constexpr int kSlots = 64;
+    void* slab = nullptr;
+    if (cudaMallocHost(&slab, kSlots * kPinnedSlot) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int k = kSlots - 1; k >= 0; --k) g_pinned_free.push_back(static_cast<char*>(slab) + k * kPinnedSlot);
+  }
+  void* q = g_pinned_free.back();
+  g_pinned_free.pop_back();
+  return q;
+}
+
+void pinned_slot_free(void* p) {
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free.push_back(p);
+}
+
 }  // namespace host
 }  // namespace hobi
 
@@ -188,7 +246,8 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
 
   HOBI_TRY(h->alloc(&h->x, 2 * h->nv));
   HOBI_TRY(h->alloc(&h->e_dev, 1));
-  HOBI_CK(cudaMallocHost(&h->host_scalar, sizeof(double)));
+  h->host_scalar = static_cast<double*>(pinned_slot());
+  if (!h->host_scalar) return fail(HOBI_ERR_NOMEM, "pinned host slot allocation failed");
   if (light) {
     HOBI_CK(cudaStreamSynchronize(h->stream));
     return HOBI_OK;
@@ -263,7 +322,9 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_TRY(h->alloc(&h->nrm, 1));
   HOBI_TRY(h->alloc(&h->dpart, (size_t)(m + 1) * kDotBlocks));
   HOBI_TRY(h->alloc(&h->st, 1));
-  HOBI_CK(cudaMallocHost(&h->st_host, sizeof(GmresState)));
+  static_assert(sizeof(GmresState) <= kPinnedSlot, "GMRES state read-back must fit a pinned slot");
+  h->st_host = static_cast<GmresState*>(pinned_slot());
+  if (!h->st_host) return fail(HOBI_ERR_NOMEM, "pinned host slot allocation failed");
   HOBI_CK(cudaMemsetAsync(h->H, 0, sizeof(double) * (m + 1) * m, h->stream));
   HOBI_CK(cudaStreamSynchronize(h->stream));
   return HOBI_OK;

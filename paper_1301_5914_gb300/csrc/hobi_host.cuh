@@ -54,6 +54,20 @@ struct DeviceGuard {
 // Analytic FP32 far-field block shape for a problem size (hobi_capi.cu).
 int choose_shape(int n_targets, int n_pad, int num_sms);
 
+// Device memory of the single-molecule handles comes from one library-owned stream-ordered pool
+// per device (cudaMemPoolCreate, no release threshold): a handle set up after another one has
+// been destroyed reuses the memory it returned instead of paying a cudaMalloc per table and a
+// device-synchronising cudaFree per table at destruction. The pool keeps what it holds until the
+// process exits. Allocations and frees are ordered on the handle's stream (hobi_capi.cu).
+cudaError_t pool_alloc(void** p, size_t bytes, int device, cudaStream_t s);
+cudaError_t pool_free(void* p, cudaStream_t s);
+// Pinned host slots of at most kPinnedSlot bytes (the GMRES state read-back, a host scalar) from
+// a process-wide free list, pinned 64 at a time and kept until the process exits: a handle does
+// not pay a cudaMallocHost / cudaFreeHost pair for them (hobi_capi.cu). nullptr on failure.
+constexpr size_t kPinnedSlot = 256;
+void* pinned_slot();
+void pinned_slot_free(void* p);
+
 }  // namespace host
 }  // namespace hobi
 
@@ -150,10 +164,10 @@ struct hobi_ctx {
     void* q = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = pool_alloc(&q, bytes, device, stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(HOBI_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+      return fail(HOBI_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
                                       cudaGetErrorString(e));
     }
     allocs.push_back(q);
@@ -164,7 +178,7 @@ struct hobi_ctx {
   void release(void* p) {
     for (auto& a : allocs)
       if (a == p) {
-        cudaFree(a);
+        pool_free(a, stream);
         a = nullptr;
       }
   }
@@ -465,13 +479,13 @@ struct hobi_ctx {
       for (auto& ev : row)
         if (ev) cudaEventDestroy(ev);
     for (void* p : allocs)
-      if (p) cudaFree(p);
+      if (p) pool_free(p, stream);
     for (auto& e : prof_ev) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
-    if (st_host) cudaFreeHost(st_host);
-    if (host_scalar) cudaFreeHost(host_scalar);
+    if (st_host) pinned_slot_free(st_host);
+    if (host_scalar) pinned_slot_free(host_scalar);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
     if (ev_t0) cudaEventDestroy(ev_t0);

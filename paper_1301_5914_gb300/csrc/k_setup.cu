@@ -13,7 +13,9 @@
 //  * right-hand side S1, S2 (Eq. (11)) with the charges' 1/eps1
 #include <math.h>
 
-#include "hobi_internal.cuh"
+#include <cmath>
+
+#include "ff_body.cuh"
 
 namespace hobi {
 namespace {
@@ -234,42 +236,52 @@ __device__ void element_points(double3 X1, double3 n1, double3 X2, double3 n2, d
   arc_point(p[4], m4, p[7], m7, 0.5, &p[9], &dummy);
 }
 
-// Cubic Lagrange interpolant on the 10 points above: value and (r,s) derivatives at (r,s).
+// Cubic Lagrange basis on the 10 points above and its (r,s) derivatives at (r,s), in point order.
 // Barycentrics l1 = 1-r-s, l2 = r, l3 = s. Vertex functions l(3l-1)(3l-2)/2, edge functions
 // 9/2 la lb (3 la - 1) for the point nearer corner a, centre 27 l1 l2 l3.
-__device__ void interpolate(const double3 p[10], double r, double s, double3* x, double3* xr, double3* xs) {
+__device__ void basis(double r, double s, double* N, double* Nr, double* Ns) {
   const double l[3] = {1.0 - r - s, r, s};
   const double dlr[3] = {-1.0, 1.0, 0.0}, dls[3] = {-1.0, 0.0, 1.0};
-  double3 X = mk(0, 0, 0), R = mk(0, 0, 0), S = mk(0, 0, 0);
   for (int a = 0; a < 3; ++a) {
     double la = l[a];
-    double f = 0.5 * la * (3.0 * la - 1.0) * (3.0 * la - 2.0);
     double df = 0.5 * (27.0 * la * la - 18.0 * la + 2.0);
-    X = X + f * p[a];
-    R = R + (df * dlr[a]) * p[a];
-    S = S + (df * dls[a]) * p[a];
+    N[a] = 0.5 * la * (3.0 * la - 1.0) * (3.0 * la - 2.0);
+    Nr[a] = df * dlr[a];
+    Ns[a] = df * dls[a];
   }
   // (near corner, far corner, point index)
   const int ep[6][3] = {{0, 1, 3}, {1, 0, 4}, {1, 2, 5}, {2, 1, 6}, {2, 0, 7}, {0, 2, 8}};
   for (int e = 0; e < 6; ++e) {
     double la = l[ep[e][0]], lb = l[ep[e][1]];
-    double f = 4.5 * la * lb * (3.0 * la - 1.0);
     double fa = 4.5 * lb * (6.0 * la - 1.0), fb = 4.5 * la * (3.0 * la - 1.0);
-    double fr = fa * dlr[ep[e][0]] + fb * dlr[ep[e][1]];
-    double fs = fa * dls[ep[e][0]] + fb * dls[ep[e][1]];
-    X = X + f * p[ep[e][2]];
-    R = R + fr * p[ep[e][2]];
-    S = S + fs * p[ep[e][2]];
+    N[ep[e][2]] = 4.5 * la * lb * (3.0 * la - 1.0);
+    Nr[ep[e][2]] = fa * dlr[ep[e][0]] + fb * dlr[ep[e][1]];
+    Ns[ep[e][2]] = fa * dls[ep[e][0]] + fb * dls[ep[e][1]];
   }
-  double f = 27.0 * l[0] * l[1] * l[2];
-  double fr = 27.0 * (l[1] * l[2] * dlr[0] + l[0] * l[2] * dlr[1] + l[0] * l[1] * dlr[2]);
-  double fs = 27.0 * (l[1] * l[2] * dls[0] + l[0] * l[2] * dls[1] + l[0] * l[1] * dls[2]);
-  X = X + f * p[9];
-  R = R + fr * p[9];
-  S = S + fs * p[9];
+  N[9] = 27.0 * l[0] * l[1] * l[2];
+  Nr[9] = 27.0 * (l[1] * l[2] * dlr[0] + l[0] * l[2] * dlr[1] + l[0] * l[1] * dlr[2]);
+  Ns[9] = 27.0 * (l[1] * l[2] * dls[0] + l[0] * l[2] * dls[1] + l[0] * l[1] * dls[2]);
+}
+
+// Interpolant value and (r,s) derivatives from basis values B = {N[10], Nr[10], Ns[10]}.
+__device__ __forceinline__ void combine_points(const double3 p[10], const double* B, double3* x, double3* xr,
+                                               double3* xs) {
+  double3 X = mk(0, 0, 0), R = mk(0, 0, 0), S = mk(0, 0, 0);
+  for (int q = 0; q < 10; ++q) {
+    X = X + B[q] * p[q];
+    R = R + B[10 + q] * p[q];
+    S = S + B[20 + q] * p[q];
+  }
   *x = X;
   *xr = R;
   *xs = S;
+}
+
+// Cubic Lagrange interpolant on the 10 points: value and (r,s) derivatives at (r,s).
+__device__ void interpolate(const double3 p[10], double r, double s, double3* x, double3* xr, double3* xs) {
+  double B[30];
+  basis(r, s, B, B + 10, B + 20);
+  combine_points(p, B, x, xr, xs);
 }
 
 // The 4-point regular rule: collapsed coordinates r = xi (1 - eta), s = xi eta; xi from the
@@ -283,19 +295,6 @@ __device__ void regular_point(int m, double* r, double* s, double* w) {
   *r = xi * (1.0 - eta);
   *s = xi * eta;
   *w = 0.5 * wx;
-}
-
-// 4-point Gauss-Legendre on [0,1]
-__device__ void gl4_point(int k, double* x, double* w) {
-  const double t = 2.0 / 7.0 * sqrt(1.2);
-  double inner = sqrt(3.0 / 7.0 - t), outer = sqrt(3.0 / 7.0 + t);
-  double win = (18.0 + sqrt(30.0)) / 72.0, wout = (18.0 - sqrt(30.0)) / 72.0;
-  switch (k) {
-    case 0: *x = 0.5 - 0.5 * outer; *w = wout; break;
-    case 1: *x = 0.5 - 0.5 * inner; *w = win; break;
-    case 2: *x = 0.5 + 0.5 * inner; *w = win; break;
-    default: *x = 0.5 + 0.5 * outer; *w = wout; break;
-  }
 }
 
 __global__ void k_node_gen(int nf, const int* F, const double* V, const double* Nv, double* elem, double* ny,
@@ -328,21 +327,36 @@ __global__ void k_node_gen(int nf, const int* F, const double* V, const double* 
 // With d = x - y, r = |d|, E = exp(-kappa r), P = E (1 + kappa r), Q = E (3 + 3 kappa r + kappa^2 r^2):
 //   4 pi K1 = (1 - E)/r,  4 pi K2 = (eps P - 1) (d.ny)/r^3,  4 pi K3 = (P/eps - 1) (d.nx)/r^3,
 //   4 pi K4 = (P - 1)(nx.ny)/r^3 - (Q - 3)(d.nx)(d.ny)/r^5.
-__device__ void kernels_fp64(double3 x, double3 nx, double3 y, double3 ny, double eps, double kappa,
-                             double K[4]) {
+// 1/r and E come from the FP64 far field's own routines (ff_body.cuh: MUFU rsqrt seed + Newton
+// step, table-driven exponential with the 256-entry table `tab` in shared memory), within a few
+// units in the last place of sqrt, division and exp.
+struct KernelConsts {
+  double eps, ieps, kappa, c256;  // c256 = -256 log2(e) kappa: E = 2^(c256 r / 256)
+};
+__device__ void kernels_fp64(double3 x, double3 nx, double3 y, double3 ny, const KernelConsts& kc,
+                             const double* tab, double K[4]) {
   double3 d = x - y;
-  double r = sqrt(dot(d, d));
-  double ir = 1.0 / r, ir2 = ir * ir, ir3 = ir2 * ir;
-  double kr = kappa * r;
-  double E = exp(-kr);
+  double r2 = dot(d, d);
+  double ir = ff::rsqrt_f64(r2);
+  double r = r2 * ir;
+  double ir2 = ir * ir, ir3 = ir2 * ir;
+  double kr = kc.kappa * r;
+  double E = ff::exp2_256th(r * kc.c256, tab);
   double P = E * (1.0 + kr);
   double Q = E * (3.0 + kr * (3.0 + kr));
   double ax = dot(d, nx), ay = dot(d, ny), c = dot(nx, ny);
   K[0] = kInv4Pi * (1.0 - E) * ir;
-  K[1] = kInv4Pi * (eps * P - 1.0) * ay * ir3;
-  K[2] = kInv4Pi * (P / eps - 1.0) * ax * ir3;
+  K[1] = kInv4Pi * (kc.eps * P - 1.0) * ay * ir3;
+  K[2] = kInv4Pi * (P * kc.ieps - 1.0) * ax * ir3;
   K[3] = kInv4Pi * ((P - 1.0) * c - (Q - 3.0) * ax * ay * ir2) * ir3;
 }
+
+// The 16-point singular rule in the (r', s') frame with the target vertex at the origin: the
+// 4 x 4 Gauss-Legendre tensor rule on [0,1]^2 under the Duffy map r' = (1 - y) x, s' = y x, with
+// the map's Jacobian x folded into the weights. Computed once on the host.
+struct SingularRule {
+  double r[16], s[16], w[16];
+};
 
 __global__ void k_vertex_of_entry(int nv, const int* ptr, int* vert) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -353,7 +367,20 @@ __global__ void k_vertex_of_entry(int nv, const int* ptr, int* vert) {
 // One thread per (vertex i, incident face j) entry.
 __global__ void k_correction(int n_entries, const int* vert, const int* F, const double* V, const double* Nv,
                              const int* inc_face, const double* elem, const double* ny, const double* nnu,
-                             const double* nW, double eps, double kappa, double* corr) {
+                             const double* nW, KernelConsts kc, SingularRule rule, double* corr) {
+  __shared__ double tab[ff::kExpTable];
+  // basis values at the 16 rule points for each of the 3 corners the target vertex can be
+  __shared__ double bt[3 * 16][30];
+  ff::exp_table_init(tab);
+  for (int t = threadIdx.x; t < 3 * 16; t += blockDim.x) {
+    const int kk = t / 16, m = t % 16;
+    double l[3];
+    l[kk] = 1.0 - rule.r[m] - rule.s[m];
+    l[(kk + 1) % 3] = rule.r[m];
+    l[(kk + 2) % 3] = rule.s[m];
+    basis(l[1], l[2], bt[t], bt[t] + 10, bt[t] + 20);
+  }
+  __syncthreads();
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_entries) return;
   int i = vert[e], j = inc_face[e];
@@ -364,33 +391,28 @@ __global__ void k_correction(int n_entries, const int* vert, const int* F, const
   for (int q = 0; q < 10; ++q) p[q] = ld3(elem + 30 * (size_t)j + 3 * q);
   double acc[3][4] = {};
   // 16-point singular rule: Duffy map with vertex i at the origin of the (r',s') frame
-  for (int a = 0; a < 4; ++a) {
-    double xa, wa;
-    gl4_point(a, &xa, &wa);
-    for (int b = 0; b < 4; ++b) {
-      double yb, wb;
-      gl4_point(b, &yb, &wb);
-      double rp = (1.0 - yb) * xa, sp = yb * xa;
-      double l[3];
-      l[k] = 1.0 - rp - sp;
-      l[(k + 1) % 3] = rp;
-      l[(k + 2) % 3] = sp;
-      double3 y, yr, ys;
-      interpolate(p, l[1], l[2], &y, &yr, &ys);
-      double3 cr = cross(yr, ys);
-      double J = sqrt(dot(cr, cr));
-      double K[4];
-      kernels_fp64(x, nx, y, (1.0 / J) * cr, eps, kappa, K);
-      double w = wa * wb * xa * J;
-      for (int n = 0; n < 3; ++n)
-        for (int q = 0; q < 4; ++q) acc[n][q] += w * l[n] * K[q];
-    }
+  for (int m = 0; m < 16; ++m) {
+    const double rp = rule.r[m], sp = rule.s[m];
+    double l[3];
+    l[k] = 1.0 - rp - sp;
+    l[(k + 1) % 3] = rp;
+    l[(k + 2) % 3] = sp;
+    double3 y, yr, ys;
+    combine_points(p, bt[16 * k + m], &y, &yr, &ys);
+    double3 cr = cross(yr, ys);
+    double J2 = dot(cr, cr);
+    double iJ = ff::rsqrt_f64(J2);
+    double K[4];
+    kernels_fp64(x, nx, y, iJ * cr, kc, tab, K);
+    double w = rule.w[m] * (J2 * iJ);
+    for (int n = 0; n < 3; ++n)
+      for (int q = 0; q < 4; ++q) acc[n][q] += w * l[n] * K[q];
   }
   // minus the regular-rule terms of the same face that the far field includes
   for (int m = 0; m < 4; ++m) {
     size_t node = 4 * (size_t)j + m;
     double K[4];
-    kernels_fp64(x, nx, ld3(ny + 3 * node), ld3(nnu + 3 * node), eps, kappa, K);
+    kernels_fp64(x, nx, ld3(ny + 3 * node), ld3(nnu + 3 * node), kc, tab, K);
     for (int n = 0; n < 3; ++n)
       for (int q = 0; q < 4; ++q) acc[n][q] -= nW[3 * node + n] * K[q];
   }
@@ -518,8 +540,27 @@ cudaError_t launch_correction_entries(int n_entries, const int* vert, const int*
                                       const double* Nv, const int* inc_face, const double* elem, const double* ny,
                                       const double* nnu, const double* nW, double eps, double kappa, double* corr,
                                       cudaStream_t s) {
-  k_correction<<<nblk(n_entries, 64), 64, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, eps,
-                                                    kappa, corr);
+  // 4-point Gauss-Legendre on [0, 1]: nodes 1/2 (1 -+ sqrt(3/7 +- (2/7) sqrt(6/5))), weights
+  // (18 -+ sqrt(30))/72 for the outer / inner pair
+  const double t = 2.0 / 7.0 * std::sqrt(1.2);
+  const double inner = std::sqrt(3.0 / 7.0 - t), outer = std::sqrt(3.0 / 7.0 + t);
+  const double win = (18.0 + std::sqrt(30.0)) / 72.0, wout = (18.0 - std::sqrt(30.0)) / 72.0;
+  const double gx[4] = {0.5 - 0.5 * outer, 0.5 - 0.5 * inner, 0.5 + 0.5 * inner, 0.5 + 0.5 * outer};
+  const double gw[4] = {wout, win, win, wout};
+  SingularRule rule;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      rule.r[4 * a + b] = (1.0 - gx[b]) * gx[a];
+      rule.s[4 * a + b] = gx[b] * gx[a];
+      rule.w[4 * a + b] = gw[a] * gw[b] * gx[a];
+    }
+  KernelConsts kc;
+  kc.eps = eps;
+  kc.ieps = 1.0 / eps;
+  kc.kappa = kappa;
+  kc.c256 = -ff::kExpTable * 1.44269504088896340735992468100 * kappa;
+  k_correction<<<nblk(n_entries, 64), 64, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, kc, rule,
+                                                    corr);
   return cudaGetLastError();
 }
 
