@@ -41,3 +41,24 @@ def test_reference_arm_line(monkeypatch):
     assert line["cpu_baseline"]["cpu_model"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["higher_is_better"] is True and line["unit"] == "pair-evals/s"
+
+
+def test_roofline_arithmetic():
+    """The lane-peak fractions the bench line reports: pairs x operations per pair / launch time
+    against SMs x lanes x clock, and the profile averages they start from."""
+    bench = _bench()
+    # 1.113e12 pairs/s at 30 FP32 operations per pair on 152 SMs x 128 lanes x 2070 MHz
+    launch_s = 12.06e-3
+    pairs = 1.113e12 * launch_s
+    achieved, peak, frac = bench.alu_fraction(launch_s, pairs, 30, 128, 152, 2070.0)
+    assert abs(peak - 152 * 128 * 2070e6) < 1.0
+    assert abs(achieved - 1.113e12 * 30) / achieved < 1e-12
+    assert abs(frac - 1.113e12 * 30 / (152 * 128 * 2070e6)) < 1e-12 and 0.82 < frac < 0.84
+    # FP64: 44 operations per pair against 2 lanes per SM
+    _, peak64, frac64 = bench.alu_fraction(1.0, 1.29e10, bench.FP64_OPS_PER_PAIR, bench.FP64_LANES_PER_SM, 152, 2070.0)
+    assert abs(peak64 - 152 * 2 * 2070e6) < 1.0 and 0.89 < frac64 < 0.91
+    # profile averages: summed milliseconds and pairs over the launch count; no launches -> no division by zero
+    s, p = bench.ff_launch_rate({"farfield_ms": 24.0, "launches": 2, "pairs": 4.0e10})
+    assert abs(s - 12e-3) < 1e-15 and p == 2.0e10
+    s0, p0 = bench.ff_launch_rate({"farfield_ms": 0.0, "launches": 0, "pairs": 0.0})
+    assert s0 == 0.0 and p0 == 0.0
