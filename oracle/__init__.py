@@ -62,7 +62,7 @@ def _load():
     lib.or_reaction_potential.argtypes = [C.c_void_p, dp, dp, C.c_int64, dp]
     lib.or_energy.argtypes = [C.c_void_p, dp]
     lib.or_energy.restype = C.c_double
-    lib.or_gmres.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, dp, dp,
+    lib.or_gmres.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp,
                              C.POINTER(C.c_int)]
     lib.or_gmres.restype = C.c_int
     lib.or_lobi_geometry.argtypes = [C.c_void_p, dp, dp, dp]
@@ -71,7 +71,8 @@ def _load():
     lib.or_lobi_rhs.argtypes = [C.c_void_p, dp]
     lib.or_lobi_energy.argtypes = [C.c_void_p, dp]
     lib.or_lobi_energy.restype = C.c_double
-    lib.or_lobi_gmres.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, dp, dp, C.POINTER(C.c_int)]
+    lib.or_lobi_gmres.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp,
+                                  C.POINTER(C.c_int)]
     lib.or_lobi_gmres.restype = C.c_int
     lib.or_regular_rule.argtypes = [dp, dp, dp]
     lib.or_gauss_legendre4.argtypes = [dp, dp]
@@ -275,16 +276,18 @@ class Problem:
         """E_sol in kcal/mol from the solution u = [phi; dphi/dnu]."""
         return float(_lib.or_energy(self._h, _p(_f64(u))))
 
-    def gmres(self, tol: float = 1e-6, max_it: int = 200, restart: int = 50, b=None):
-        """Returns (u, iterations, converged, residual history)."""
+    def gmres(self, tol: float = 1e-6, max_it: int = 200, restart: int = 50, b=None, scaled: bool = True):
+        """Returns (u, iterations, converged, residual history). scaled: GMRES on the unknowns
+        scaled by the inverse diagonal coefficients (1/2)(1 + eps), (1/2)(1 + 1/eps) of the two
+        row blocks (right preconditioning; the residual test is that of A u = b)."""
         if b is None:
             b = self.rhs()
         b = _f64(b)
         x = np.zeros(2 * self.nv)
         hist = np.zeros(max_it + 1)
         conv = C.c_int(0)
-        it = _lib.or_gmres(self._h, _p(b), float(tol), int(max_it), int(restart), _p(x), _p(hist),
-                           C.byref(conv))
+        it = _lib.or_gmres(self._h, _p(b), float(tol), int(max_it), int(restart), int(bool(scaled)), _p(x),
+                           _p(hist), C.byref(conv))
         return x, int(it), bool(conv.value), hist[: it + 1].copy()
 
 
@@ -329,15 +332,15 @@ class LobiProblem(Problem):
     def energy(self, u) -> float:
         return float(_lib.or_lobi_energy(self._h, _p(_f64(u))))
 
-    def gmres(self, tol: float = 1e-6, max_it: int = 200, restart: int = 50, b=None):
+    def gmres(self, tol: float = 1e-6, max_it: int = 200, restart: int = 50, b=None, scaled: bool = True):
         if b is None:
             b = self.rhs()
         b = _f64(b)
         x = np.zeros(2 * self.nf)
         hist = np.zeros(max_it + 1)
         conv = C.c_int(0)
-        it = _lib.or_lobi_gmres(self._h, _p(b), float(tol), int(max_it), int(restart), _p(x), _p(hist),
-                                C.byref(conv))
+        it = _lib.or_lobi_gmres(self._h, _p(b), float(tol), int(max_it), int(restart), int(bool(scaled)), _p(x),
+                                _p(hist), C.byref(conv))
         return x, int(it), bool(conv.value), hist[: it + 1].copy()
 
 

@@ -546,11 +546,15 @@ double or_energy(const or_ctx* c, const double* u) {
 /* Solves A x = b (n unknowns, A applied by op) from x0 = 0; stops when
  * ||b - A x||_2 / ||b||_2 <= tol (the Givens residual estimate) or after max_it
  * matvecs. Returns the iteration count; resid[k] (if non-NULL, length max_it+1)
- * holds the relative residual estimate after k iterations. */
+ * holds the relative residual estimate after k iterations.
+ * dscale (NULL: none): GMRES runs on A D x' = b with x = D x', D = diag(dscale), i.e.
+ * each Arnoldi step applies A to D v and the update is x += D (V y); the residual and the
+ * stopping test stay those of A x = b (reading: the unknowns scaled by the inverse of the
+ * diagonal coefficients of Eqs. (17)-(20)). */
 typedef void (*or_operator)(const or_ctx* c, const double* u, double* Au);
 
 static int gmres_core(const or_ctx* c, or_operator op, int64_t n, const double* b, double tol, int max_it,
-                      int restart, double* x, double* resid, int* converged) {
+                      int restart, const double* dscale, double* x, double* resid, int* converged) {
   int m = restart;
   double* Vb = (double*)malloc(sizeof(double) * n * (m + 1));
   double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));
@@ -559,6 +563,7 @@ static int gmres_core(const or_ctx* c, or_operator op, int64_t n, const double* 
   double* g = (double*)malloc(sizeof(double) * (m + 1));
   double* w = (double*)malloc(sizeof(double) * n);
   double* y = (double*)malloc(sizeof(double) * m);
+  double* z = (double*)malloc(sizeof(double) * n);
   double bnorm = 0.0;
   for (int64_t i = 0; i < n; ++i) bnorm += b[i] * b[i];
   bnorm = sqrt(bnorm);
@@ -579,7 +584,12 @@ static int gmres_core(const or_ctx* c, or_operator op, int64_t n, const double* 
     g[0] = beta;
     int k;
     for (k = 0; k < m && it < max_it; ++k) {
-      op(c, &Vb[n * k], w);
+      if (dscale) {
+        for (int64_t i = 0; i < n; ++i) z[i] = dscale[i] * Vb[n * k + i];
+        op(c, z, w);
+      } else {
+        op(c, &Vb[n * k], w);
+      }
       ++it;
       for (int jj = 0; jj <= k; ++jj) {
         double h = 0.0;
@@ -617,18 +627,38 @@ static int gmres_core(const or_ctx* c, or_operator op, int64_t n, const double* 
       for (int jj = ii + 1; jj < k; ++jj) t -= H[ii * m + jj] * y[jj];
       y[ii] = t / H[ii * m + ii];
     }
-    for (int jj = 0; jj < k; ++jj)
-      for (int64_t i = 0; i < n; ++i) x[i] += y[jj] * Vb[n * jj + i];
+    if (dscale) {
+      for (int64_t i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int jj = 0; jj < k; ++jj) t += y[jj] * Vb[n * jj + i];
+        x[i] += dscale[i] * t;
+      }
+    } else {
+      for (int jj = 0; jj < k; ++jj)
+        for (int64_t i = 0; i < n; ++i) x[i] += y[jj] * Vb[n * jj + i];
+    }
     if (*converged) break;
   }
 done:
-  free(Vb); free(H); free(cs); free(sn); free(g); free(w); free(y);
+  free(Vb); free(H); free(cs); free(sn); free(g); free(w); free(y); free(z);
   return it;
 }
 
-int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int restart, double* x, double* resid,
-             int* converged) {
-  return gmres_core(c, or_matvec, 2 * c->nv, b, tol, max_it, restart, x, resid, converged);
+/* The inverse diagonal coefficients of the two row blocks of Eqs. (17)-(20) (and (21)-(22)):
+ * 1 / ((1/2)(1 + eps)) for the first half of the unknowns, 1 / ((1/2)(1 + 1/eps)) for the second. */
+static double* diag_scale(const or_ctx* c, int64_t n) {
+  double* d = (double*)malloc(sizeof(double) * n);
+  for (int64_t i = 0; i < n; ++i) d[i] = i < n / 2 ? 1.0 / (0.5 * (1.0 + c->eps)) : 1.0 / (0.5 * (1.0 + 1.0 / c->eps));
+  return d;
+}
+
+int or_gmres(const or_ctx* c, const double* b, double tol, int max_it, int restart, int scaled, double* x,
+             double* resid, int* converged) {
+  const int64_t n = 2 * c->nv;
+  double* d = scaled ? diag_scale(c, n) : NULL;
+  int it = gmres_core(c, or_matvec, n, b, tol, max_it, restart, d, x, resid, converged);
+  free(d);
+  return it;
 }
 
 /* ------------------------------------------------------------------ */
@@ -724,9 +754,13 @@ double or_lobi_energy(const or_ctx* c, const double* u) {
   return 0.5 * 4.0 * OR_PI * 332.0716 * e;
 }
 
-int or_lobi_gmres(const or_ctx* c, const double* b, double tol, int max_it, int restart, double* x, double* resid,
-                  int* converged) {
-  return gmres_core(c, or_lobi_matvec, 2 * c->nf, b, tol, max_it, restart, x, resid, converged);
+int or_lobi_gmres(const or_ctx* c, const double* b, double tol, int max_it, int restart, int scaled, double* x,
+                  double* resid, int* converged) {
+  const int64_t n = 2 * c->nf;
+  double* d = scaled ? diag_scale(c, n) : NULL;
+  int it = gmres_core(c, or_lobi_matvec, n, b, tol, max_it, restart, d, x, resid, converged);
+  free(d);
+  return it;
 }
 
 int or_num_threads(void) {
