@@ -99,6 +99,13 @@ typedef struct {
   double fast_theta;   /* treecode admissibility parameter in (0, 1] (default 0.7): a source
                           cluster C of more than (n+1)^3 nodes acts on a target batch B through its
                           (n+1)^3 Chebyshev proxy points when r_B + r_C < theta |c_B - c_C| */
+  int32_t gmres_scaling; /* 1 (default): GMRES works on the unknowns scaled by the inverse of the
+                            diagonal coefficients (1/2)(1 + eps) and (1/2)(1 + 1/eps) of the two row
+                            blocks of Eqs. (17)-(20) (right preconditioning by that constant diagonal;
+                            the residual and the stopping test stay those of A u = b). The paper
+                            states no scaling; its Table 3 reports 9-13 iterations for a protein,
+                            which the scaled system reproduces on molecules and the unscaled one
+                            (about three times as many) does not. 0: unscaled GMRES. */
 } hobi_options;
 
 typedef struct {

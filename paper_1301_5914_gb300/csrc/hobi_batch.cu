@@ -32,6 +32,9 @@ struct hobi_batch_ctx {
   double *b = nullptr, *x = nullptr, *w = nullptr, *Vb = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr;
   double *g = nullptr, *y = nullptr, *hcol = nullptr, *cvec = nullptr, *nrm = nullptr, *dpart = nullptr;
   double *u_stage = nullptr, *au_stage = nullptr;
+  int gmres_scaling = 1;      // GMRES on the D^-1-scaled unknowns of each molecule
+  double* dscale = nullptr;   // [N] scale factor per unknown (gmres_scaling)
+  double* zvec = nullptr;     // [N] D^-1 times the current Arnoldi vector
   BatchState* gs = nullptr;
   MolState* ms = nullptr;
   BatchState* gs_host = nullptr;  // pinned
@@ -135,7 +138,13 @@ struct hobi_batch_ctx {
   static constexpr int kIterationKernels = 14;
   int iteration() {
     const int m = restart;
-    HOBI_TRY(matvec(Vb, &gs->k, N, w, ms));
+    if (gmres_scaling) {  // w = A D^-1 v_k on every active molecule
+      HOBI_CK(launch_scale_column(Vb, N, &gs->k, dscale, zvec, N, stream));
+      if (!capturing) launches += 1;
+      HOBI_TRY(matvec(zvec, nullptr, 0, w, ms));
+    } else {
+      HOBI_TRY(matvec(Vb, &gs->k, N, w, ms));
+    }
     for (int pass = 0; pass < 2; ++pass) {
       HOBI_CK(launch_bdots(Vb, N, w, seg, nseg, gs, ms, 0, dpart, stream));
       HOBI_CK(launch_breduce(dpart, nseg, mol_seg, nmol, m, gs, ms, 0, ldc(), cvec, hcol, pass, stream));
@@ -177,7 +186,7 @@ struct hobi_batch_ctx {
       prof_pending = true;
     }
     HOBI_CK(cudaGraphLaunch(gx, stream));
-    launches += kIterationKernels + (pi && nfup > 0 ? 2 : 0);
+    launches += kIterationKernels + (pi && nfup > 0 ? 2 : 0) + (gmres_scaling ? 1 : 0);
     return HOBI_OK;
   }
   int read_state() {
@@ -241,6 +250,7 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   so.restart = 1;      // the batch owns the Krylov workspace
   so.use_graph = 0;
   so.fast_degree = 0;  // the batch decides per molecule and builds the plans below
+  so.gmres_scaling = 0;
   for (int m = 0; m < nmol; ++m) {
     const int64_t nv = v_off[m + 1] - v_off[m], nf = f_off[m + 1] - f_off[m], nc = c_off[m + 1] - c_off[m];
     hobi_t h = nullptr;
@@ -389,6 +399,14 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   HOBI_TRY(B->alloc(&B->cvec, (size_t)nmol * (m + 1)));
   HOBI_TRY(B->alloc(&B->nrm, (size_t)nmol * (m + 1)));
   HOBI_TRY(B->alloc(&B->dpart, (size_t)(m + 1) * B->nseg));
+  if (B->gmres_scaling) {  // per molecule: 1/((1+eps)/2) on the first n_v unknowns, 1/((1+1/eps)/2) on the rest
+    HOBI_TRY(B->alloc(&B->dscale, B->N));
+    HOBI_TRY(B->alloc(&B->zvec, B->N));
+    for (int i = 0; i < nmol; ++i)
+      HOBI_CK(launch_fill_scale(B->dscale + B->mols_h[i].u_off, B->mols_h[i].nv, 1.0 / (0.5 * (1.0 + B->eps)),
+                                1.0 / (0.5 * (1.0 + 1.0 / B->eps)), B->stream));
+    B->launches += nmol;
+  }
   HOBI_TRY(B->alloc(&B->gs, 1));
   HOBI_TRY(B->alloc(&B->ms, nmol));
   HOBI_CK(cudaMallocHost(&B->gs_host, sizeof(BatchState)));
@@ -435,6 +453,7 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
     return fail(HOBI_ERR_ARG, "fast_theta must be in (0, 1]");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
+  if (o.gmres_scaling != 0 && o.gmres_scaling != 1) return fail(HOBI_ERR_ARG, "gmres_scaling must be 0 or 1");
   int dev = o.device;
   if (dev < 0) {
     cudaError_t e = cudaGetDevice(&dev);
@@ -454,6 +473,7 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
   B->kappa = kappa;
   B->fast_degree = o.fast_degree;
   B->fast_theta = o.fast_theta;
+  B->gmres_scaling = o.gmres_scaling;
   int r = HOBI_OK;
   do {
     cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
@@ -552,7 +572,8 @@ int hobi_solve_batch(hobi_batch_t B, double tol, int32_t max_it, double* phi, do
       HOBI_TRY(B->read_state());
       if (B->all_done()) break;
     }
-    HOBI_CK(launch_bfinish(B->H, m, B->g, B->ms, nmol, B->y, B->Vb, B->N, B->seg, B->nseg, B->x, B->stream));
+    HOBI_CK(launch_bfinish(B->H, m, B->g, B->ms, nmol, B->y, B->Vb, B->N, B->seg, B->nseg, B->x, B->dscale,
+                              B->stream));
     B->launches += 2;
     if (B->all_done() || it >= max_it) break;
     // restart the unconverged molecules from r = b - A x

@@ -317,6 +317,13 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_TRY(h->alloc(&h->g, m + 1));
   HOBI_TRY(h->alloc(&h->y, m));
   HOBI_TRY(h->alloc(&h->w, n));
+  if (h->gmres_scaling) {  // D^-1 per unknown and the scaled Arnoldi vector (reading 21)
+    HOBI_TRY(h->alloc(&h->dscale, n));
+    HOBI_TRY(h->alloc(&h->zvec, n));
+    HOBI_CK(launch_fill_scale(h->dscale, h->nv, 1.0 / (0.5 * (1.0 + h->eps)), 1.0 / (0.5 * (1.0 + 1.0 / h->eps)),
+                              h->stream));
+    h->launches += 1;
+  }
   HOBI_TRY(h->alloc(&h->hcol, m + 1));
   HOBI_TRY(h->alloc(&h->cvec, m + 1));
   HOBI_TRY(h->alloc(&h->nrm, 1));
@@ -347,6 +354,7 @@ void hobi_default_options(hobi_options* opt) {
   opt->ff_shape = -1;
   opt->fast_degree = 0;
   opt->fast_theta = 0.7;
+  opt->gmres_scaling = 1;
 }
 
 const char* hobi_last_error(void) { return g_err.c_str(); }
@@ -385,6 +393,7 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
     return fail(HOBI_ERR_ARG, "fast summation is implemented for the HOBI scheme only");
   if (o.restart <= 0) o.restart = 50;
   if (o.restart > 200) return fail(HOBI_ERR_ARG, "restart must be <= 200");
+  if (o.gmres_scaling != 0 && o.gmres_scaling != 1) return fail(HOBI_ERR_ARG, "gmres_scaling must be 0 or 1");
 
   int dev = o.device;
   if (dev < 0) {
@@ -404,6 +413,7 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   h->ff_shape = o.ff_shape;
   h->fast_degree = o.fast_degree;
   h->fast_theta = o.fast_theta;
+  h->gmres_scaling = o.gmres_scaling;
   h->nv = n_v;
   h->nf = n_f;
   h->nc = n_c;
@@ -550,7 +560,7 @@ int solve_impl(hobi_t h, const double* u0, bool warm, double tol, int32_t max_it
       hist.push_back(h->st_host->rel);
       if (h->st_host->converged || h->st_host->breakdown) break;
     }
-    HOBI_CK(launch_finish_cycle(h->H, m, h->g, h->st, h->y, h->Vb, n, h->x, n, h->stream));
+    HOBI_CK(launch_finish_cycle(h->H, m, h->g, h->st, h->y, h->Vb, n, h->x, n, h->dscale, h->stream));
     h->launches += 2;
     if (h->st_host->converged || h->st_host->breakdown || h->st_host->it >= max_it) break;
     // restart from r = b - A x

@@ -158,6 +158,9 @@ struct hobi_ctx {
   // kernels in one GMRES iteration: gather, far field, combine, 2 x (dots, reduce, axpy),
   // norm dots + reduce, Givens, next basis vector, advance
   static constexpr int kIterationKernels = 14;
+  int gmres_scaling = 1;        // reading 21: GMRES on D^-1-scaled unknowns
+  double* dscale = nullptr;     // [2 n_v] the scale factor of each unknown (gmres_scaling)
+  double* zvec = nullptr;       // [2 n_v] D^-1 times the current Arnoldi vector
 
   template <class T>
   int alloc(T** p, size_t count) {
@@ -373,7 +376,13 @@ struct hobi_ctx {
   int iteration() {
     const int64_t n = 2 * nv;
     const int m = restart;
-    HOBI_TRY(matvec_dev(Vb, &st->k, n, w));
+    if (gmres_scaling) {  // w = A D^-1 v_k (right preconditioning by the constant diagonal)
+      HOBI_CK(launch_scale_column(Vb, n, &st->k, dscale, zvec, n, stream));
+      if (!capturing) launches += 1;
+      HOBI_TRY(matvec_dev(zvec, nullptr, 0, w));
+    } else {
+      HOBI_TRY(matvec_dev(Vb, &st->k, n, w));
+    }
     for (int pass = 0; pass < 2; ++pass) {
       HOBI_CK(launch_dots(Vb, n, w, n, st, 0, dpart, stream));
       HOBI_CK(launch_reduce_dots(dpart, m, st, 0, cvec, hcol, pass, stream));
@@ -412,7 +421,7 @@ struct hobi_ctx {
       }
     }
     HOBI_CK(cudaGraphLaunch(gx, stream));
-    launches += kIterationKernels + (fast_active(pi) ? 2 : 0);
+    launches += kIterationKernels + (fast_active(pi) ? 2 : 0) + (gmres_scaling ? 1 : 0);
     if (prof) {
       replay_prof_pending = true;
       replay_prof_pi = pi;

@@ -181,8 +181,15 @@ cudaError_t launch_next_basis(double* Vb, int64_t ld, const double* w, int64_t n
 cudaError_t launch_advance(GmresState* st, cudaStream_t s);
 cudaError_t launch_cycle_start(double* Vb, int64_t n, const double* nrm2, GmresState* st, double* g, int m,
                                int first, cudaStream_t s);
+// x += D (V y) with D = diag(dscale), or x += V y when dscale is null
 cudaError_t launch_finish_cycle(const double* H, int m, const double* g, const GmresState* st, double* y,
-                                const double* Vb, int64_t ld, double* x, int64_t n, cudaStream_t s);
+                                const double* Vb, int64_t ld, double* x, int64_t n, const double* dscale,
+                                cudaStream_t s);
+// z = diag(dscale) V_(*kptr) (the Arnoldi vector on the scaled unknowns)
+cudaError_t launch_scale_column(const double* Vb, int64_t ld, const int* kptr, const double* dscale, double* z,
+                                int64_t n, cudaStream_t s);
+// d[i] = lo for i < half, hi for half <= i < 2 half
+cudaError_t launch_fill_scale(double* d, int64_t half, double lo, double hi, cudaStream_t s);
 cudaError_t launch_residual_start(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t s);
 // mixed-precision refinement: x += d; out[0] = ||v||_2 (device scalar)
 cudaError_t launch_add_in_place(double* x, const double* d, int64_t n, cudaStream_t s);
@@ -326,7 +333,8 @@ cudaError_t launch_badvance(BatchState* gs, cudaStream_t s);
 cudaError_t launch_bcycle_start(double* Vb, const Segment* seg, int nseg, BatchState* gs, MolState* ms, int nmol,
                                 const double* nrm, int ldc, double* g, int m, int first, cudaStream_t s);
 cudaError_t launch_bfinish(const double* H, int m, const double* g, const MolState* ms, int nmol, double* y,
-                           const double* Vb, int64_t ld, const Segment* seg, int nseg, double* x, cudaStream_t s);
+                           const double* Vb, int64_t ld, const Segment* seg, int nseg, double* x,
+                           const double* dscale, cudaStream_t s);
 cudaError_t launch_bresidual(const double* b, const double* Ax, double* r, const Segment* seg, int nseg,
                              const MolState* ms, cudaStream_t s);
 

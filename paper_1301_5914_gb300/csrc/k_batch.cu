@@ -290,7 +290,8 @@ __global__ void k_bbacksolve(const double* H, int m, const double* g, const MolS
 }
 
 __global__ void k_bupdate_x(const double* __restrict__ Vb, int64_t ld, const double* __restrict__ y, int m,
-                            const Segment* __restrict__ seg, int nseg, const MolState* ms, double* __restrict__ x) {
+                            const Segment* __restrict__ seg, int nseg, const MolState* ms, double* __restrict__ x,
+                            const double* __restrict__ dscale) {
   for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
     const Segment sg = seg[s];
     const int k = ms[sg.mol].cols;
@@ -298,9 +299,15 @@ __global__ void k_bupdate_x(const double* __restrict__ Vb, int64_t ld, const dou
     const double* ym = y + (size_t)sg.mol * m;
     for (int i = threadIdx.x; i < sg.len; i += blockDim.x) {
       const int64_t gi = sg.start + i;
-      double acc = x[gi];
-      for (int j = 0; j < k; ++j) acc += ym[j] * Vb[(int64_t)j * ld + gi];
-      x[gi] = acc;
+      if (dscale) {  // scaled unknowns: x += D (V y)
+        double t = 0.0;
+        for (int j = 0; j < k; ++j) t += ym[j] * Vb[(int64_t)j * ld + gi];
+        x[gi] += dscale[gi] * t;
+      } else {
+        double acc = x[gi];
+        for (int j = 0; j < k; ++j) acc += ym[j] * Vb[(int64_t)j * ld + gi];
+        x[gi] = acc;
+      }
     }
   }
 }
@@ -407,9 +414,10 @@ cudaError_t launch_bcycle_start(double* Vb, const Segment* seg, int nseg, BatchS
 }
 
 cudaError_t launch_bfinish(const double* H, int m, const double* g, const MolState* ms, int nmol, double* y,
-                           const double* Vb, int64_t ld, const Segment* seg, int nseg, double* x, cudaStream_t s) {
+                           const double* Vb, int64_t ld, const Segment* seg, int nseg, double* x,
+                           const double* dscale, cudaStream_t s) {
   k_bbacksolve<<<nblk(nmol, 64), 64, 0, s>>>(H, m, g, ms, nmol, y);
-  k_bupdate_x<<<seg_grid(nseg), kThreads, 0, s>>>(Vb, ld, y, m, seg, nseg, ms, x);
+  k_bupdate_x<<<seg_grid(nseg), kThreads, 0, s>>>(Vb, ld, y, m, seg, nseg, ms, x, dscale);
   return cudaGetLastError();
 }
 

@@ -150,15 +150,34 @@ __global__ void k_backsolve(const double* H, int m, const double* g, const Gmres
   }
 }
 
-// x += sum_{j<k} y_j V_j
+// x += sum_{j<k} y_j V_j, or with scaled unknowns x += dscale * sum_{j<k} y_j V_j
 __global__ void k_update_x(const double* __restrict__ Vb, int64_t ld, const double* __restrict__ y,
-                           const GmresState* st, double* __restrict__ x, int64_t n) {
+                           const GmresState* st, double* __restrict__ x, int64_t n, const double* __restrict__ dscale) {
   const int k = st->k;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = x[i];
-    for (int j = 0; j < k; ++j) s += y[j] * Vb[(int64_t)j * ld + i];
-    x[i] = s;
+    if (dscale) {
+      double t = 0.0;
+      for (int j = 0; j < k; ++j) t += y[j] * Vb[(int64_t)j * ld + i];
+      x[i] += dscale[i] * t;
+    } else {
+      double s = x[i];
+      for (int j = 0; j < k; ++j) s += y[j] * Vb[(int64_t)j * ld + i];
+      x[i] = s;
+    }
   }
+}
+
+// z = dscale * V_k (k from device memory)
+__global__ void k_scale_column(const double* __restrict__ Vb, int64_t ld, const int* kptr,
+                               const double* __restrict__ dscale, double* __restrict__ z, int64_t n) {
+  const double* v = Vb + (int64_t)(*kptr) * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = dscale[i] * v[i];
+}
+
+__global__ void k_fill_scale(double* __restrict__ d, int64_t half, double lo, double hi) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * half; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = i < half ? lo : hi;
 }
 
 __global__ void k_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
@@ -229,9 +248,21 @@ cudaError_t launch_cycle_start(double* Vb, int64_t n, const double* nrm2, GmresS
 }
 
 cudaError_t launch_finish_cycle(const double* H, int m, const double* g, const GmresState* st, double* y,
-                                const double* Vb, int64_t ld, double* x, int64_t n, cudaStream_t s) {
+                                const double* Vb, int64_t ld, double* x, int64_t n, const double* dscale,
+                                cudaStream_t s) {
   k_backsolve<<<1, 32, 0, s>>>(H, m, g, st, y);
-  k_update_x<<<grid_for(n), kThreads, 0, s>>>(Vb, ld, y, st, x, n);
+  k_update_x<<<grid_for(n), kThreads, 0, s>>>(Vb, ld, y, st, x, n, dscale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_column(const double* Vb, int64_t ld, const int* kptr, const double* dscale, double* z,
+                                int64_t n, cudaStream_t s) {
+  k_scale_column<<<grid_for(n), kThreads, 0, s>>>(Vb, ld, kptr, dscale, z, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_scale(double* d, int64_t half, double lo, double hi, cudaStream_t s) {
+  k_fill_scale<<<grid_for(2 * half), kThreads, 0, s>>>(d, half, lo, hi);
   return cudaGetLastError();
 }
 

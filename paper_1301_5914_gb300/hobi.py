@@ -54,7 +54,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mem_device", C.c_int32), ("stream", C.c_void_p),
                 ("restart", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32), ("scheme", C.c_int32),
                 ("autotune", C.c_int32), ("ff_shape", C.c_int32), ("fast_degree", C.c_int32),
-                ("fast_theta", C.c_double)]
+                ("fast_theta", C.c_double), ("gmres_scaling", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -196,13 +196,15 @@ class Solver:
     (host mode) or all CUDA torch tensors (device mode). scheme "hobi" (the paper's method) or
     "lobi" (its low-order comparison scheme: unknowns at the n_f face centroids). fast_degree > 0
     replaces the FP32 far field by a treecode of that interpolation degree with admissibility
-    parameter fast_theta (hobi_options.fast_degree / fast_theta).
+    parameter fast_theta (hobi_options.fast_degree / fast_theta). gmres_scaling (default True) runs
+    GMRES on the unknowns scaled by the inverse diagonal coefficients of the two row blocks;
+    False runs it on A u = b as it stands (hobi_options.gmres_scaling).
     """
 
     def __init__(self, V, F, N, charges, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
                  restart: int = 50, use_graph: bool = True, device: int | None = None, stream=None,
                  scheme: str = "hobi", autotune: bool = True, ff_shape: int = -1, fast_degree: int = 0,
-                 fast_theta: float = 0.7):
+                 fast_theta: float = 0.7, gmres_scaling: bool = True):
         lib = load_library()
         self._lib = lib
         self.device_mode = _is_cuda_tensor(V)
@@ -216,6 +218,7 @@ class Solver:
         opt.ff_shape = int(ff_shape)
         opt.fast_degree = int(fast_degree)
         opt.fast_theta = float(fast_theta)
+        opt.gmres_scaling = 1 if gmres_scaling else 0
         if self.device_mode:
             import torch
 
@@ -453,11 +456,12 @@ class BatchSolver:
     concatenated inputs are first placed in CUDA torch tensors (device-pointer mode).
     fast_degree > 0: molecules with at least 4096 collocation points whose treecode plan pays off
     use fast summation for the FP32 far field (hobi_options.fast_degree / fast_theta).
+    gmres_scaling as for Solver.
     """
 
     def __init__(self, molecules, eps1: float, eps2: float, kappa: float, precision: str = "fp32",
                  restart: int = 50, use_graph: bool = True, device_mode: bool = False, stream=None,
-                 device_arrays=None, fast_degree: int = 0, fast_theta: float = 0.7):
+                 device_arrays=None, fast_degree: int = 0, fast_theta: float = 0.7, gmres_scaling: bool = True):
         lib = load_library()
         self._lib = lib
         if len(molecules) == 0:
@@ -483,6 +487,7 @@ class BatchSolver:
         opt.use_graph = 1 if use_graph else 0
         opt.fast_degree = int(fast_degree)
         opt.fast_theta = float(fast_theta)
+        opt.gmres_scaling = 1 if gmres_scaling else 0
         if self.device_mode:
             import torch
 

@@ -59,6 +59,8 @@ def _setup(lib, mesh, nv=None, nf=None, nc=None, eps1=1.0, eps2=80.0, kappa=0.1,
     (dict(fast_degree=4, fast_theta=math.nan), "fast_theta"),
     (dict(fast_degree=4, scheme=hobi.HOBI_SCHEME_LOBI), "HOBI scheme only"),
     (dict(restart=201), "restart"),
+    (dict(gmres_scaling=2), "gmres_scaling"),
+    (dict(gmres_scaling=-1), "gmres_scaling"),
 ])
 def test_setup_rejects_invalid_input(lib, mesh, kw, msg):
     rc, err, h = _setup(lib, mesh, **kw)
@@ -122,6 +124,7 @@ def _setup_batch(lib, mesh, n_mol=2, voff=None, foff=None, qoff=None, charges=Tr
     (dict(fast_degree=12), "fast_degree"),
     (dict(fast_degree=5, fast_theta=2.0), "fast_theta"),
     (dict(restart=500), "restart"),
+    (dict(gmres_scaling=3), "gmres_scaling"),
 ])
 def test_setup_batch_rejects_invalid_input(lib, mesh, kw, msg):
     rc, err, h = _setup_batch(lib, mesh, **kw)

@@ -68,6 +68,17 @@ def test_batch_fp64_against_oracle(molecules):
         assert abs(E[i] - orc.energy(u_ref)) <= 1e-10 * abs(E[i])
 
 
+def test_batch_unscaled_gmres_against_oracle(molecules):
+    """gmres_scaling off: each molecule takes the oracle's iterations on the plain system."""
+    bs = hobi.BatchSolver(molecules[:3], EPS1, EPS2, KAPPA, precision="fp64", gmres_scaling=False)
+    phis, dphis, info = bs.solve(1e-6, 200)
+    for i, (V, F, N, Q) in enumerate(molecules[:3]):
+        orc = oracle.Problem(V, F, N, Q, EPS1, EPS2, KAPPA)
+        u_ref, it_ref, conv, _ = orc.gmres(1e-6, scaled=False)
+        assert info["iterations"][i] == it_ref
+        assert _rel(np.concatenate([phis[i], dphis[i]]), u_ref) <= 1e-10
+
+
 def test_batch_matvec_and_device_mode(molecules):
     import torch
 

@@ -137,14 +137,16 @@ def test_matvec_deterministic_and_graph_free_equal(problems):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("scaled", [True, False], ids=["scaled", "unscaled"])
 @pytest.mark.parametrize("name", ["c1_l3", "c2_l4"])
-def test_solve_fp64_matches_oracle(problems, name):
-    """Same Krylov iterations as the oracle (x0 = 0): solutions agree to 1e-10."""
+def test_solve_fp64_matches_oracle(problems, name, scaled):
+    """Same Krylov iterations as the oracle (x0 = 0), on the diagonally scaled unknowns and on
+    the plain system: solutions agree to 1e-10, residual histories to 1e-8."""
     p = problems[name]
     orc = p[-1]
-    u_ref, it_ref, conv, hist_ref = orc.gmres(1e-6)
+    u_ref, it_ref, conv, hist_ref = orc.gmres(1e-6, scaled=scaled)
     assert conv
-    s = _solver(p, "fp64")
+    s = _solver(p, "fp64", gmres_scaling=scaled)
     phi, dphi, info = s.solve(1e-6, 200, history=64)
     assert info["converged"] and info["iterations"] == it_ref
     u = np.concatenate([phi, dphi])
@@ -220,11 +222,12 @@ def test_graph_replay_equals_direct_launches(problems):
     assert np.array_equal(pa, pb) and np.array_equal(da, db)
 
 
-def test_restarted_gmres_matches_oracle(problems):
+@pytest.mark.parametrize("scaled", [True, False], ids=["scaled", "unscaled"])
+def test_restarted_gmres_matches_oracle(problems, scaled):
     p = problems["c1_l3"]
     orc = p[-1]
-    u_ref, it_ref, conv, _ = orc.gmres(1e-9, max_it=200, restart=4)
-    s = _solver(p, "fp64", restart=4)
+    u_ref, it_ref, conv, _ = orc.gmres(1e-9, max_it=200, restart=4, scaled=scaled)
+    s = _solver(p, "fp64", restart=4, gmres_scaling=scaled)
     phi, dphi, info = s.solve(1e-9, 200)
     assert info["converged"] and info["iterations"] == it_ref
     assert _rel(np.concatenate([phi, dphi]), u_ref) <= 1e-9

@@ -35,6 +35,7 @@ def test_library_builds_loads_and_exports():
     hobi._lib.hobi_default_options(C.byref(opt))
     assert opt.precision == hobi.HOBI_FP32_BULK and opt.restart == 50 and opt.use_graph == 1
     assert opt.fast_degree == 0 and abs(opt.fast_theta - 0.7) < 1e-15
+    assert opt.gmres_scaling == 1  # GMRES on the diagonally scaled unknowns by default
     assert isinstance(hobi._lib.hobi_last_error(), bytes)  # thread-local message of the last failing call
 
 
