@@ -2,6 +2,9 @@
 // same eps1, eps2, kappa solved together. Each molecule's tables come from a single-molecule
 // handle (hobi_host.cuh); the batch owns the concatenated Krylov workspace, the far-field task
 // lists and the captured GMRES iteration.
+#include <atomic>
+#include <thread>
+
 #include "hobi_host.cuh"
 
 // =============================================================================================
@@ -20,7 +23,7 @@ struct hobi_batch_ctx {
   int* ff_err = nullptr;  // far-field tile pipeline timeout flag (device)
   std::vector<int64_t> vert_off_h, node_off_h, charge_off_h;
   int64_t N = 0, total_nodes = 0, total_verts = 0;
-  std::vector<void*> allocs;
+  DeviceArena arena;  // the batch's buffers and its member handles' tables
   MolDesc* mols = nullptr;
   FFTask *tasks[2] = {nullptr, nullptr};
   int ntasks[2] = {0, 0};
@@ -80,12 +83,12 @@ struct hobi_batch_ctx {
     void* q = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = arena.get(&q, bytes, stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(HOBI_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+      return fail(HOBI_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                      cudaGetErrorString(e));
     }
-    allocs.push_back(q);
     *p = static_cast<T*>(q);
     return HOBI_OK;
   }
@@ -227,10 +230,9 @@ struct hobi_batch_ctx {
         if (gx) cudaGraphExecDestroy(gx);
     for (cudaEvent_t e : pev)
       if (e) cudaEventDestroy(e);
-    for (void* p : allocs)
-      if (p) cudaFree(p);
     for (hobi_t s : subs)
       if (s) delete s;
+    arena.release_all(stream);  // after the members: their last work is ordered before this
     if (gs_host) cudaFreeHost(gs_host);
     if (ms_host) cudaFreeHost(ms_host);
     for (cudaEvent_t e : {ev_in, ev_out, ev_t0, ev_t1})
@@ -240,6 +242,8 @@ struct hobi_batch_ctx {
 };
 
 namespace {
+
+constexpr int kSetupThreads = 8;  // host threads that build a batch's member handles
 
 int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v_off, const int32_t* faces,
                      const int64_t* f_off, const double* normals, const double* charges, const int64_t* c_off,
@@ -251,14 +255,30 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   so.use_graph = 0;
   so.fast_degree = 0;  // the batch decides per molecule and builds the plans below
   so.gmres_scaling = 0;
-  for (int m = 0; m < nmol; ++m) {
-    const int64_t nv = v_off[m + 1] - v_off[m], nf = f_off[m + 1] - f_off[m], nc = c_off[m + 1] - c_off[m];
-    hobi_t h = nullptr;
-    int r = create_handle(vertices + 3 * v_off[m], nv, faces + 3 * f_off[m], nf, normals + 3 * v_off[m],
-                          nc > 0 ? charges + 4 * c_off[m] : nullptr, nc, eps1, eps2, B->kappa, &so, true, &h);
-    if (r != HOBI_OK) return fail(r, "molecule " + std::to_string(m) + ": " + g_err);
-    B->subs.push_back(h);
-  }
+  // The members are independent: host threads build them concurrently, each on its own stream,
+  // so their small kernels and host round trips overlap. Every handle made is kept (the batch's
+  // destructor frees them); the first failing molecule in index order is reported.
+  std::vector<hobi_t> made(nmol, nullptr);
+  std::vector<int> rc(nmol, HOBI_OK);
+  std::vector<std::string> msg(nmol);
+  std::atomic<int> next{0};
+  auto build = [&]() {
+    for (int m = next.fetch_add(1); m < nmol; m = next.fetch_add(1)) {
+      const int64_t nv = v_off[m + 1] - v_off[m], nf = f_off[m + 1] - f_off[m], nc = c_off[m + 1] - c_off[m];
+      rc[m] = create_handle(vertices + 3 * v_off[m], nv, faces + 3 * f_off[m], nf, normals + 3 * v_off[m],
+                            nc > 0 ? charges + 4 * c_off[m] : nullptr, nc, eps1, eps2, B->kappa, &so, true,
+                            &made[m], &B->arena);
+      if (rc[m] != HOBI_OK) msg[m] = g_err;
+    }
+  };
+  const int nthreads = std::min(nmol, kSetupThreads);
+  std::vector<std::thread> workers;
+  for (int t = 1; t < nthreads; ++t) workers.emplace_back(build);
+  build();
+  for (auto& t : workers) t.join();
+  B->subs = made;
+  for (int m = 0; m < nmol; ++m)
+    if (rc[m] != HOBI_OK) return fail(rc[m], "molecule " + std::to_string(m) + ": " + msg[m]);
   // descriptors, partial-sum buffers and the far-field task lists (one per precision)
   B->vert_off_h.assign(nmol + 1, 0);
   B->node_off_h.assign(nmol + 1, 0);
@@ -463,6 +483,10 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
   DeviceGuard guard(dev);
   hobi_batch_ctx* B = new hobi_batch_ctx();
   B->device = dev;
+  B->arena.device = dev;
+  B->arena.chunk = size_t(32) << 20;  // one arena for all members: larger blocks
+  B->arena.direct = size_t(8) << 20;
+  B->arena.shared = true;
   B->user_stream = static_cast<cudaStream_t>(o.stream);
   B->mem_device = o.mem_device ? 1 : 0;
   B->precision = o.precision;
@@ -486,6 +510,7 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
       r = fail(HOBI_ERR_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(e));
       break;
     }
+    B->arena.home = B->stream;
     r = B->enter();
     if (r != HOBI_OK) break;
     r = batch_setup_impl(B, vertices, vertex_offsets, faces, face_offsets, vertex_normals, charges, charge_offsets, eps1,

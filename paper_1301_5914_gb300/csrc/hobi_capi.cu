@@ -44,6 +44,58 @@ cudaError_t pool_alloc(void** p, size_t bytes, int device, cudaStream_t s) {
 
 cudaError_t pool_free(void* p, cudaStream_t s) { return cudaFreeAsync(p, s); }
 
+cudaError_t DeviceArena::get(void** p, size_t bytes, cudaStream_t s) {
+  constexpr size_t kAlign = 256;
+  bytes = (bytes + kAlign - 1) / kAlign * kAlign;
+  std::unique_lock<std::mutex> lock(mu, std::defer_lock);
+  if (shared) lock.lock();
+  const cudaStream_t as = shared ? home : s;
+  auto new_block = [&](void** q, size_t n) {
+    cudaError_t e = pool_alloc(q, n, device, as);
+    if (e == cudaSuccess && shared) e = cudaStreamSynchronize(home);
+    return e;
+  };
+  if (bytes >= direct) {
+    cudaError_t e = new_block(p, bytes);
+    if (e == cudaSuccess) own.push_back(*p);
+    return e;
+  }
+  if (bytes > left) {
+    void* c = nullptr;
+    cudaError_t e = new_block(&c, chunk);
+    if (e != cudaSuccess) return e;
+    chunks.push_back(c);
+    cur = static_cast<char*>(c);
+    left = chunk;
+  }
+  *p = cur;
+  cur += bytes;
+  left -= bytes;
+  return cudaSuccess;
+}
+
+void DeviceArena::put(void* p, cudaStream_t s) {
+  std::unique_lock<std::mutex> lock(mu, std::defer_lock);
+  if (shared) lock.lock();
+  for (size_t i = 0; i < own.size(); ++i)
+    if (own[i] == p) {
+      pool_free(p, s);
+      own.erase(own.begin() + i);
+      return;
+    }
+}
+
+void DeviceArena::release_all(cudaStream_t s) {
+  std::unique_lock<std::mutex> lock(mu, std::defer_lock);
+  if (shared) lock.lock();
+  for (void* b : chunks) pool_free(b, s);
+  for (void* b : own) pool_free(b, s);
+  chunks.clear();
+  own.clear();
+  cur = nullptr;
+  left = 0;
+}
+
 void* pinned_slot() {
   std::lock_guard<std::mutex> lock(g_pinned_mu);
   if (g_pinned_free.empty()) {
@@ -365,7 +417,7 @@ namespace hobi {
 namespace host {
 int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int64_t n_f, const double* vertex_normals,
                   const double* charges, int64_t n_c, double eps1, double eps2, double kappa, const hobi_options* opt,
-                  bool light, hobi_t* out) {
+                  bool light, hobi_t* out, DeviceArena* arena) {
   g_err.clear();
   if (!out) return fail(HOBI_ERR_ARG, "out handle pointer is NULL");
   *out = nullptr;
@@ -403,6 +455,8 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   DeviceGuard guard(dev);
   hobi_ctx* h = new hobi_ctx();
   h->device = dev;
+  h->own_arena.device = dev;
+  if (arena) h->arena = arena;
   h->user_stream = static_cast<cudaStream_t>(o.stream);
   h->mem_device = o.mem_device ? 1 : 0;
   h->precision = o.precision;

@@ -61,6 +61,29 @@ int choose_shape(int n_targets, int n_pad, int num_sms);
 // process exits. Allocations and frees are ordered on the handle's stream (hobi_capi.cu).
 cudaError_t pool_alloc(void** p, size_t bytes, int device, cudaStream_t s);
 cudaError_t pool_free(void* p, cudaStream_t s);
+
+// The device buffers of one handle, or of a whole batch with its member handles. Buffers smaller
+// than `direct` bytes are carved (256-byte aligned) from blocks of `chunk` bytes; larger ones get
+// a block of their own. Every block is one stream-ordered allocation from the pool above, so a
+// handle makes a few pool calls instead of one per table: once the pool holds thousands of freed
+// blocks each call costs about 0.1 ms on the host (measured on GB300 with 64-molecule batches).
+// A carved buffer is returned with the whole arena; put() returns an own-block buffer at once.
+// A shared arena (a batch's, used by its members' streams from several host threads) locks, and
+// allocates its blocks on the `home` stream and waits for them, so every block is ready for use
+// on any stream.
+struct DeviceArena {
+  int device = 0;
+  size_t chunk = size_t(4) << 20, direct = size_t(1) << 20;
+  bool shared = false;
+  cudaStream_t home = nullptr;
+  std::mutex mu;
+  std::vector<void*> chunks, own;  // carved-from blocks; buffers with a block of their own
+  char* cur = nullptr;
+  size_t left = 0;
+  cudaError_t get(void** p, size_t bytes, cudaStream_t s);
+  void put(void* p, cudaStream_t s);
+  void release_all(cudaStream_t s);
+};
 // Pinned host slots of at most kPinnedSlot bytes (the GMRES state read-back, a host scalar) from
 // a process-wide free list, pinned 64 at a time and kept until the process exits: a handle does
 // not pay a cudaMallocHost / cudaFreeHost pair for them (hobi_capi.cu). nullptr on failure.
@@ -117,7 +140,8 @@ struct hobi_ctx {
   std::vector<FastTask> fast_tasks_h;  // host copies, for a batch that merges this molecule's plan
   std::vector<FastUpItem> fast_up_h;
   std::vector<int64_t> fast_task_cost_h;  // source entries of each task
-  std::vector<void*> allocs;
+  DeviceArena own_arena;
+  DeviceArena* arena = &own_arena;  // a batch member carves its tables from the batch's arena
   // inputs and geometry
   double *V = nullptr, *Nin = nullptr, *Nv = nullptr, *Q = nullptr;
   int *F = nullptr, *deg = nullptr, *inc_ptr = nullptr, *inc_face = nullptr, *entry_vertex = nullptr;
@@ -167,24 +191,17 @@ struct hobi_ctx {
     void* q = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = pool_alloc(&q, bytes, device, stream);
+    cudaError_t e = arena->get(&q, bytes, stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(HOBI_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
                                       cudaGetErrorString(e));
     }
-    allocs.push_back(q);
     *p = static_cast<T*>(q);
     return HOBI_OK;
   }
 
-  void release(void* p) {
-    for (auto& a : allocs)
-      if (a == p) {
-        pool_free(a, stream);
-        a = nullptr;
-      }
-  }
+  void release(void* p) { arena->put(p, stream); }
 
   // enter: work on the internal stream starts after everything already queued on the user stream
   int enter() {
@@ -487,8 +504,7 @@ struct hobi_ctx {
     for (auto& row : gev)
       for (auto& ev : row)
         if (ev) cudaEventDestroy(ev);
-    for (void* p : allocs)
-      if (p) pool_free(p, stream);
+    own_arena.release_all(stream);
     for (auto& e : prof_ev) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
@@ -507,8 +523,10 @@ namespace hobi {
 namespace host {
 // Validates the inputs, copies them to the device and builds every table of one molecule
 // (hobi_setup); light = 1 skips the per-molecule Krylov workspace and graphs (batch members).
+// A non-null arena (a batch's) holds the handle's device buffers instead of its own arena; it
+// must outlive the handle.
 int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int64_t n_f, const double* vertex_normals,
                   const double* charges, int64_t n_c, double eps1, double eps2, double kappa, const hobi_options* opt,
-                  bool light, hobi_t* out);
+                  bool light, hobi_t* out, DeviceArena* arena = nullptr);
 }  // namespace host
 }  // namespace hobi

@@ -421,6 +421,9 @@ __global__ void k_correction(int n_entries, const int* vert, const int* F, const
 }
 
 // ------------------------------------------------------------------ right-hand side (Eq. (11))
+// One thread per vertex sums G0 and its normal derivative over all charges (staged 256 at a time
+// in shared memory). 1/r comes from the far field's FP64 reciprocal square root (a MUFU seed and
+// one second-order Newton step), not from sqrt and a division: 19 FP64 operations per pair.
 __global__ void k_rhs(int nv, int nc, const double* V, const double* Nv, const double* Q, double eps1,
                       double* b) {
   __shared__ double sq[256 * 4];
@@ -437,12 +440,11 @@ __global__ void k_rhs(int nv, int nc, const double* V, const double* Nv, const d
     for (int t = threadIdx.x; t < 4 * cnt; t += blockDim.x) sq[t] = Q[4 * (size_t)base + t];
     __syncthreads();
     for (int k = 0; k < cnt; ++k) {
-      double3 d = x - mk(sq[4 * k], sq[4 * k + 1], sq[4 * k + 2]);
-      double q = sq[4 * k + 3];
-      double r = sqrt(dot(d, d));
-      double ir = 1.0 / r;
-      s1 += q * ir;
-      s2 -= q * dot(d, n) * ir * ir * ir;
+      const double3 d = x - mk(sq[4 * k], sq[4 * k + 1], sq[4 * k + 2]);
+      const double ir = ff::rsqrt_f64(dot(d, d));
+      const double qir = sq[4 * k + 3] * ir;
+      s1 += qir;
+      s2 = fma(-qir * (ir * ir), dot(d, n), s2);
     }
   }
   if (i < nv) {
