@@ -116,3 +116,35 @@ def test_batch_reports_bad_member():
     with pytest.raises(hobi.HobiError) as ei:
         hobi.BatchSolver([(V, F, N, Q), (V, F[:-1], N, Q)], 1.0, 80.0, 0.0)
     assert ei.value.code == hobi.HOBI_ERR_MESH and "molecule 1" in str(ei.value)
+
+
+def test_concurrent_member_setup_is_deterministic(molecules):
+    """Members are built by several host threads on their own streams and carve their tables from
+    one shared arena (in whatever order the threads reach it): two set-ups of the same batch give
+    bit-identical solutions and energies."""
+    mols = molecules * 3  # 15 members: more than the set-up threads
+    out = []
+    for _ in range(2):
+        bs = hobi.BatchSolver(mols, EPS1, EPS2, KAPPA, precision="fp32")
+        phis, dphis, info = bs.solve(1e-6, 200)
+        out.append((np.concatenate(phis + dphis), bs.energy(), info["iterations"].copy()))
+        bs.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    # the copies of one molecule in the batch give the same result as each other
+    n = len(molecules)
+    assert np.array_equal(out[0][1][:n], out[0][1][n:2 * n])
+
+
+def test_batch_reports_first_bad_member_in_index_order():
+    """With several invalid members built concurrently, the error names the first one."""
+    V, F, N = synth.icosphere(2, 2.0)
+    Q = synth.point_charge(0, 0, 0, 1.0)
+    good, bad = (V, F, N, Q), (V, F[:-1], N, Q)
+    mols = [good] * 12
+    mols[3] = bad
+    mols[9] = bad
+    for _ in range(3):
+        with pytest.raises(hobi.HobiError) as ei:
+            hobi.BatchSolver(mols, 1.0, 80.0, 0.0)
+        assert ei.value.code == hobi.HOBI_ERR_MESH and "molecule 3:" in str(ei.value)
