@@ -660,12 +660,13 @@ int hobi_energy_batch(hobi_batch_t B, double* e_sol) {
                             B->stream));
   }
   HOBI_CK(cudaStreamSynchronize(B->stream));
+  // queue every member's energy on its own stream, then wait for each
   for (int i = 0; i < B->nmol; ++i) {
     hobi_t h = B->subs[i];
     h->have_solution = true;
-    HOBI_TRY(hobi_energy(h, &e_sol[i]));
-    B->launches += h->nc > 0 ? 4 : 0;
+    HOBI_TRY(energy_enqueue(h));
   }
+  for (int i = 0; i < B->nmol; ++i) HOBI_TRY(energy_finish(B->subs[i], &e_sol[i]));
   return HOBI_OK;
 }
 

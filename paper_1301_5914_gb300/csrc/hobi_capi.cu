@@ -503,6 +503,31 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
   *out = h;
   return HOBI_OK;
 }
+// Eq. (23): the reaction potential at the charges and the weighted sum, queued on the handle's
+// stream with the scalar's copy to pinned host memory; energy_finish waits and reads it. Split so
+// that a batch can queue all its members before waiting for any.
+int energy_enqueue(hobi_ctx* h) {
+  if (h->nc == 0) return HOBI_OK;
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->ensure_point_buffers(h->nc));
+  HOBI_TRY(h->reaction_dev(h->nc, h->ctgt32, h->ctgt64, h->phi_pts));
+  HOBI_CK(launch_energy_sum((int)h->nc, h->Q, h->phi_pts, h->e_dev, h->stream));
+  h->launches += 1;
+  HOBI_CK(cudaMemcpyAsync(h->host_scalar, h->e_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return h->leave();
+}
+
+int energy_finish(hobi_ctx* h, double* e_sol) {
+  if (h->nc == 0) {
+    *e_sol = 0.0;
+    return HOBI_OK;
+  }
+  HOBI_CK(cudaStreamSynchronize(h->stream));
+  HOBI_TRY(h->collect_profile());
+  HOBI_TRY(h->check_farfield());
+  *e_sol = *h->host_scalar;
+  return HOBI_OK;
+}
 }  // namespace host
 }  // namespace hobi
 
@@ -813,22 +838,8 @@ int hobi_energy(hobi_t h, double* e_sol) {
   if (!h || !e_sol) return fail(HOBI_ERR_ARG, "NULL argument");
   if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
   DeviceGuard guard(h->device);
-  if (h->nc == 0) {
-    *e_sol = 0.0;
-    return HOBI_OK;
-  }
-  HOBI_TRY(h->enter());
-  HOBI_TRY(h->ensure_point_buffers(h->nc));
-  HOBI_TRY(h->reaction_dev(h->nc, h->ctgt32, h->ctgt64, h->phi_pts));
-  HOBI_CK(launch_energy_sum((int)h->nc, h->Q, h->phi_pts, h->e_dev, h->stream));
-  h->launches += 1;
-  HOBI_CK(cudaMemcpyAsync(h->host_scalar, h->e_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  HOBI_TRY(h->leave());
-  HOBI_CK(cudaStreamSynchronize(h->stream));
-  HOBI_TRY(h->collect_profile());
-  HOBI_TRY(h->check_farfield());
-  *e_sol = *h->host_scalar;
-  return HOBI_OK;
+  HOBI_TRY(energy_enqueue(h));
+  return energy_finish(h, e_sol);
 }
 
 int hobi_get_nodes(hobi_t h, double* y, double* nu, double* W) {

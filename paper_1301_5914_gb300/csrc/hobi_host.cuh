@@ -528,5 +528,8 @@ namespace host {
 int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int64_t n_f, const double* vertex_normals,
                   const double* charges, int64_t n_c, double eps1, double eps2, double kappa, const hobi_options* opt,
                   bool light, hobi_t* out, DeviceArena* arena = nullptr);
+// hobi_energy in two parts: queue the work on the handle's stream, then wait and read E_sol.
+int energy_enqueue(hobi_ctx* h);
+int energy_finish(hobi_ctx* h, double* e_sol);
 }  // namespace host
 }  // namespace hobi

@@ -568,7 +568,9 @@ cudaError_t launch_correction_entries(int n_entries, const int* vert, const int*
 
 cudaError_t launch_rhs(int nv, int nc, const double* V, const double* Nv, const double* Q, double eps1, double* b,
                        cudaStream_t s) {
-  k_rhs<<<nblk(nv, 256), 256, 0, s>>>(nv, nc, V, Nv, Q, eps1, b);
+  // one-warp blocks: a large molecule spreads over all SMs in one wave (the FP64 pipe needs only a
+  // warp or two per SM sub-partition), instead of 1-2 blocks of 256 per SM with a ragged second wave
+  k_rhs<<<nblk(nv, 32), 32, 0, s>>>(nv, nc, V, Nv, Q, eps1, b);
   return cudaGetLastError();
 }
 
