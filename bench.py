@@ -399,7 +399,7 @@ def _dev(arrays, dev):
 
 
 def extra_workload(hobi, name, dev, stream, sms, fmax, fp64_sample=4):
-    """One more BASELINE configuration, measured outside the timed region: its FP32 far-field rate
+    """One more benchmark workload, measured outside the timed region: its FP32 far-field rate
     and lane-peak fraction in a GMRES solve to 1e-6, the solve time, and the FP32-bulk solution
     against the FP64 operator's (mixed-precision refinement to 1e-10 on the FP64 far field; for a
     batch, on `fp64_sample` sampled molecules). Plain FP64 GMRES on these sizes runs for minutes
@@ -728,7 +728,7 @@ def run_ours(args):
                    "sample_1_thread": f"{max(8, args.cpu_rows // 16)} rows ({pairs1:.3g} pairs, {dt1:.1f} s)",
                    # the oracle's time for the whole timed step at its measured rate (pairs / rate)
                    "step_s_extrapolated": pairs_per_step / val}
-        # the larger BASELINE configurations (outside the timed region)
+        # the larger benchmark workloads (outside the timed region)
         extra = None
         if args.workload == "c2l6" and not args.no_extra and ws == 1:
             extra = {}

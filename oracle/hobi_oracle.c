@@ -20,15 +20,16 @@
  *   Sec. 2.5  the solvation energy (Eq. (23));
  *   GMRES     (Sec. 1 abstract; the iteration loop of the Table 1 pseudocode, Sec. 2.6).
  *
- * Readings where the paper is silent or inconsistent (each listed in the
- * design notes): eps = eps2/eps1; S1,S2 carry 1/eps1; the diagonal term is
- * counted once; the regular rule is the degree-3 collapsed Gauss-Jacobi x
+ * Readings where the paper is silent or inconsistent: eps = eps2/eps1; S1,S2
+ * carry 1/eps1; the diagonal term is counted once; the regular rule is the degree-3 collapsed Gauss-Jacobi x
  * Gauss-Legendre product; the edge arc is a cubic Hermite curve whose end
  * tangents are the chord projected onto each end's tangent plane, scaled to
  * the chord length; curve normals are the normalised linear blend of the end
  * normals made orthogonal to the curve tangent; densities are interpolated
  * linearly from the three vertices (the n=1..3 sum); the target normal is
- * the input vertex normal.
+ * the input vertex normal; GMRES runs by default on the unknowns scaled by
+ * the inverse diagonal coefficients (1/2)(1+eps) and (1/2)(1+1/eps) (right
+ * preconditioning by that constant diagonal; the paper states none).
  *
  * Parity: pinned by the tests (quadrature exactness, shape functions,
  * kernels vs finite differences, Born/Kirkwood spheres, the kappa=0

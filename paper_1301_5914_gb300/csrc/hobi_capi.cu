@@ -369,7 +369,7 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
   HOBI_TRY(h->alloc(&h->g, m + 1));
   HOBI_TRY(h->alloc(&h->y, m));
   HOBI_TRY(h->alloc(&h->w, n));
-  if (h->gmres_scaling) {  // D^-1 per unknown and the scaled Arnoldi vector (reading 21)
+  if (h->gmres_scaling) {  // D^-1 per unknown (inverse diagonal coefficients) and the scaled Arnoldi vector
     HOBI_TRY(h->alloc(&h->dscale, n));
     HOBI_TRY(h->alloc(&h->zvec, n));
     HOBI_CK(launch_fill_scale(h->dscale, h->nv, 1.0 / (0.5 * (1.0 + h->eps)), 1.0 / (0.5 * (1.0 + 1.0 / h->eps)),

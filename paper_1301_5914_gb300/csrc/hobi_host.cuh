@@ -182,7 +182,7 @@ struct hobi_ctx {
   // kernels in one GMRES iteration: gather, far field, combine, 2 x (dots, reduce, axpy),
   // norm dots + reduce, Givens, next basis vector, advance
   static constexpr int kIterationKernels = 14;
-  int gmres_scaling = 1;        // reading 21: GMRES on D^-1-scaled unknowns
+  int gmres_scaling = 1;        // GMRES on the unknowns scaled by D^-1 (hobi_options.gmres_scaling)
   double* dscale = nullptr;     // [2 n_v] the scale factor of each unknown (gmres_scaling)
   double* zvec = nullptr;       // [2 n_v] D^-1 times the current Arnoldi vector
 

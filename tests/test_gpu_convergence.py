@@ -95,7 +95,7 @@ def test_c2_errors_fall_at_first_order_in_density(c2_ladder):
     assert _order(d, e_dphi) >= 0.85
 
 
-def test_c2_fp32_bulk_within_north_star_bounds_of_fp64(c2_ladder):
+def test_c2_fp32_bulk_within_its_tolerances_of_fp64(c2_ladder):
     for L in LEVELS:
         r = c2_ladder[L]["fp32_vs_fp64"]
         assert r["phi"] <= 1e-4 and r["dphi"] <= 1e-4 and r["E"] <= 1e-5, (L, r)

@@ -359,7 +359,7 @@ def test_gmres_matches_dense_lu(scaled):
 
 
 def test_scaled_gmres_iterations_in_table3_band():
-    """Reading 21: GMRES runs on the unknowns scaled by the inverse diagonal coefficients
+    """GMRES runs on the unknowns scaled by the inverse diagonal coefficients
     (1/2)(1 + eps), (1/2)(1 + 1/eps). Table 3 reports 9-13 GMRES iterations for protein 1ajj
     (eps1 = 2 in this build's molecules) at every density. On a synthetic molecule the scaled
     system needs a count in that band and the unscaled one about three times as many (measured
