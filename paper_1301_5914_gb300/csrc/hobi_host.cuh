@@ -464,9 +464,11 @@ struct hobi_ctx {
     return HOBI_OK;
   }
 
+  // Point buffers grow at least geometrically: a carved buffer that is outgrown stays in the
+  // arena until the handle is destroyed, so the held memory stays below twice the largest need.
   int ensure_point_buffers(int64_t np) {
     if ((size_t)np <= pts_cap) return HOBI_OK;
-    size_t cap = (size_t)np < 64 ? 64 : (size_t)np;
+    const size_t cap = std::max<size_t>({(size_t)64, (size_t)np, 2 * pts_cap});
     if (ptgt32) { release(ptgt32); release(ptgt64); release(phi_pts); release(pts_in); }
     HOBI_TRY(alloc(&ptgt32, 2 * cap));
     HOBI_TRY(alloc(&ptgt64, 8 * cap));
@@ -477,6 +479,7 @@ struct hobi_ctx {
   }
   int ensure_ppart(size_t elems) {
     if (elems <= ppart_elems) return HOBI_OK;
+    elems = std::max(elems, 2 * ppart_elems);
     if (ppart) release(ppart);
     HOBI_TRY(alloc(&ppart, elems));
     ppart_elems = elems;

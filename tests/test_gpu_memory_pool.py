@@ -56,3 +56,26 @@ def test_repeated_setup_does_not_grow_device_memory():
     free1, _ = torch.cuda.mem_get_info()
     # one level-5 handle holds a few tens of MB; ten more set-ups must reuse it
     assert free0 - free1 < 64 * 1024 * 1024, (free0 - free1) / 2**20
+
+
+def test_growing_point_counts_keep_device_memory_bounded():
+    """Reaction potentials at slowly growing point counts: the point buffers grow geometrically,
+    so 300 calls from 2,000 to 2,299 points re-allocate a few times, not 300 times."""
+    import torch
+
+    V, F, N = synth.icosphere(4, 10.0)
+    Q = synth.ball_charges(10, 8.0, 2)
+    s = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32")
+    s.solve(1e-6, 200)
+    pts = synth.ball_charges(2400, 7.0, 5)[:, :3]
+    ref = s.reaction_potential(pts[:2000])
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for n in range(2000, 2300):
+        out = s.reaction_potential(pts[:n])
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    # the plan's source chunks depend on the point count: equal up to FP32 sum order
+    assert np.max(np.abs(out[:2000] - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert free0 - free1 < 32 * 1024 * 1024, (free0 - free1) / 2**20
+    s.close()
