@@ -364,7 +364,7 @@ __global__ void k_vertex_of_entry(int nv, const int* ptr, int* vert) {
   for (int e = ptr[i]; e < ptr[i + 1]; ++e) vert[e] = i;
 }
 
-// One thread per (vertex i, incident face j) entry.
+// One thread per (vertex i, incident face j) entry; a grid smaller than the entry count strides.
 __global__ void k_correction(int n_entries, const int* vert, const int* F, const double* V, const double* Nv,
                              const int* inc_face, const double* elem, const double* ny, const double* nnu,
                              const double* nW, KernelConsts kc, SingularRule rule, double* corr) {
@@ -381,43 +381,43 @@ __global__ void k_correction(int n_entries, const int* vert, const int* F, const
     basis(l[1], l[2], bt[t], bt[t] + 10, bt[t] + 20);
   }
   __syncthreads();
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_entries) return;
-  int i = vert[e], j = inc_face[e];
-  const int* f = F + 3 * j;
-  int k = (f[0] == i) ? 0 : ((f[1] == i) ? 1 : 2);
-  double3 x = ld3(V + 3 * i), nx = ld3(Nv + 3 * i);
-  double3 p[10];
-  for (int q = 0; q < 10; ++q) p[q] = ld3(elem + 30 * (size_t)j + 3 * q);
-  double acc[3][4] = {};
-  // 16-point singular rule: Duffy map with vertex i at the origin of the (r',s') frame
-  for (int m = 0; m < 16; ++m) {
-    const double rp = rule.r[m], sp = rule.s[m];
-    double l[3];
-    l[k] = 1.0 - rp - sp;
-    l[(k + 1) % 3] = rp;
-    l[(k + 2) % 3] = sp;
-    double3 y, yr, ys;
-    combine_points(p, bt[16 * k + m], &y, &yr, &ys);
-    double3 cr = cross(yr, ys);
-    double J2 = dot(cr, cr);
-    double iJ = ff::rsqrt_f64(J2);
-    double K[4];
-    kernels_fp64(x, nx, y, iJ * cr, kc, tab, K);
-    double w = rule.w[m] * (J2 * iJ);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_entries; e += gridDim.x * blockDim.x) {
+    int i = vert[e], j = inc_face[e];
+    const int* f = F + 3 * j;
+    int k = (f[0] == i) ? 0 : ((f[1] == i) ? 1 : 2);
+    double3 x = ld3(V + 3 * i), nx = ld3(Nv + 3 * i);
+    double3 p[10];
+    for (int q = 0; q < 10; ++q) p[q] = ld3(elem + 30 * (size_t)j + 3 * q);
+    double acc[3][4] = {};
+    // 16-point singular rule: Duffy map with vertex i at the origin of the (r',s') frame
+    for (int m = 0; m < 16; ++m) {
+      const double rp = rule.r[m], sp = rule.s[m];
+      double l[3];
+      l[k] = 1.0 - rp - sp;
+      l[(k + 1) % 3] = rp;
+      l[(k + 2) % 3] = sp;
+      double3 y, yr, ys;
+      combine_points(p, bt[16 * k + m], &y, &yr, &ys);
+      double3 cr = cross(yr, ys);
+      double J2 = dot(cr, cr);
+      double iJ = ff::rsqrt_f64(J2);
+      double K[4];
+      kernels_fp64(x, nx, y, iJ * cr, kc, tab, K);
+      double w = rule.w[m] * (J2 * iJ);
+      for (int n = 0; n < 3; ++n)
+        for (int q = 0; q < 4; ++q) acc[n][q] += w * l[n] * K[q];
+    }
+    // minus the regular-rule terms of the same face that the far field includes
+    for (int m = 0; m < 4; ++m) {
+      size_t node = 4 * (size_t)j + m;
+      double K[4];
+      kernels_fp64(x, nx, ld3(ny + 3 * node), ld3(nnu + 3 * node), kc, tab, K);
+      for (int n = 0; n < 3; ++n)
+        for (int q = 0; q < 4; ++q) acc[n][q] -= nW[3 * node + n] * K[q];
+    }
     for (int n = 0; n < 3; ++n)
-      for (int q = 0; q < 4; ++q) acc[n][q] += w * l[n] * K[q];
+      for (int q = 0; q < 4; ++q) corr[12 * (size_t)e + 4 * n + q] = acc[n][q];
   }
-  // minus the regular-rule terms of the same face that the far field includes
-  for (int m = 0; m < 4; ++m) {
-    size_t node = 4 * (size_t)j + m;
-    double K[4];
-    kernels_fp64(x, nx, ld3(ny + 3 * node), ld3(nnu + 3 * node), kc, tab, K);
-    for (int n = 0; n < 3; ++n)
-      for (int q = 0; q < 4; ++q) acc[n][q] -= nW[3 * node + n] * K[q];
-  }
-  for (int n = 0; n < 3; ++n)
-    for (int q = 0; q < 4; ++q) corr[12 * (size_t)e + 4 * n + q] = acc[n][q];
 }
 
 // ------------------------------------------------------------------ right-hand side (Eq. (11))
@@ -541,7 +541,7 @@ cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double*
 cudaError_t launch_correction_entries(int n_entries, const int* vert, const int* F, const double* V,
                                       const double* Nv, const int* inc_face, const double* elem, const double* ny,
                                       const double* nnu, const double* nW, double eps, double kappa, double* corr,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, int warps) {
   // 4-point Gauss-Legendre on [0, 1]: nodes 1/2 (1 -+ sqrt(3/7 +- (2/7) sqrt(6/5))), weights
   // (18 -+ sqrt(30))/72 for the outer / inner pair
   const double t = 2.0 / 7.0 * std::sqrt(1.2);
@@ -561,8 +561,12 @@ cudaError_t launch_correction_entries(int n_entries, const int* vert, const int*
   kc.ieps = 1.0 / eps;
   kc.kappa = kappa;
   kc.c256 = -ff::kExpTable * 1.44269504088896340735992468100 * kappa;
-  k_correction<<<nblk(n_entries, 64), 64, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, kc, rule,
-                                                    corr);
+  if (n_entries <= 0) return cudaSuccess;
+  if (warps > 0)
+    k_correction<<<warps, 32, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, kc, rule, corr);
+  else
+    k_correction<<<nblk(n_entries, 64), 64, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, kc, rule,
+                                                      corr);
   return cudaGetLastError();
 }
 

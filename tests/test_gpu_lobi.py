@@ -56,6 +56,17 @@ def test_lobi_matvec(case):
     assert _rel(s.matvec(u), ref) <= 1e-5
 
 
+def test_lobi_unscaled_gmres_matches_oracle(case):
+    """LOBI-PB with gmres_scaling off: the oracle's iterations and solution on the plain system."""
+    V, F, N, Q, e1, e2, ka, orc = case
+    u_ref, it_ref, conv, hist_ref = orc.gmres(1e-6, scaled=False)
+    s = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp64", scheme="lobi", gmres_scaling=False)
+    phi, dphi, info = s.solve(1e-6, history=64)
+    assert conv and info["iterations"] == it_ref
+    assert _rel(np.concatenate([phi, dphi]), u_ref) <= 1e-10
+    assert np.allclose(info["history"], hist_ref, rtol=1e-8, atol=0)
+
+
 def test_lobi_solve_and_energy(case):
     V, F, N, Q, e1, e2, ka, orc = case
     u_ref, it_ref, conv, _ = orc.gmres(1e-6)
