@@ -60,6 +60,7 @@ def _load():
     lib.or_matvec_rows.argtypes = [C.c_void_p, dp, lp, C.c_int64, dp]
     lib.or_rhs.argtypes = [C.c_void_p, dp]
     lib.or_reaction_potential.argtypes = [C.c_void_p, dp, dp, C.c_int64, dp]
+    lib.or_reaction_field.argtypes = [C.c_void_p, dp, dp, C.c_int64, dp]
     lib.or_energy.argtypes = [C.c_void_p, dp]
     lib.or_energy.restype = C.c_double
     lib.or_gmres.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp,
@@ -270,6 +271,14 @@ class Problem:
         pts = _f64(points).reshape(-1, 3)
         out = np.zeros(pts.shape[0])
         _lib.or_reaction_potential(self._h, _p(u), _p(pts), pts.shape[0], _p(out))
+        return out
+
+    def reaction_field(self, u, points) -> np.ndarray:
+        """-grad phi_reac at the points, [n, 3] (the gradient of reaction_potential)."""
+        u = _f64(u)
+        pts = _f64(points).reshape(-1, 3)
+        out = np.zeros((pts.shape[0], 3))
+        _lib.or_reaction_field(self._h, _p(u), _p(pts), pts.shape[0], _p(out))
         return out
 
     def energy(self, u) -> float:

@@ -525,6 +525,51 @@ void or_reaction_potential(const or_ctx* c, const double* u, const double* pts, 
   }
 }
 
+/* Reaction field -grad_x phi_reac at points x (the gradient of the Sec. 2.5 reaction potential
+ * with respect to the point, same regular rule): with d = x - y, r = |d|, a = d.ny,
+ *   grad G0 = -d/(4 pi r^3),  grad Gk = -E(1 + kr) d/(4 pi r^3),
+ *   grad dG0/dny = [ny - 3 a d/r^2]/(4 pi r^3),
+ *   grad dGk/dny = [E(1 + kr) ny - kappa^2 E a d - 3 E(1 + kr) a d/r^2]/(4 pi r^3)
+ * (d/dr of E(1 + kr) is -kappa^2 r E), so grad K1 = grad G0 - grad Gk and
+ * grad K2 = eps grad dGk/dny - grad dG0/dny. field[3k + c] for point k, component c. */
+static void or_kernel_grads(const double* x, const double* y, const double* ny, double eps, double kappa,
+                            double g1[3], double g2[3]) {
+  double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+  double r = norm3(d);
+  double a = dot3(d, ny);
+  double E = exp(-kappa * r);
+  double P = E * (1.0 + kappa * r);
+  double r3 = r * r * r;
+  for (int c = 0; c < 3; ++c) {
+    double gG0 = -d[c] / (4.0 * OR_PI * r3);
+    double gGk = -P * d[c] / (4.0 * OR_PI * r3);
+    double gdG0 = (ny[c] - 3.0 * a * d[c] / (r * r)) / (4.0 * OR_PI * r3);
+    double gdGk = (P * ny[c] - kappa * kappa * E * a * d[c] - 3.0 * P * a * d[c] / (r * r)) / (4.0 * OR_PI * r3);
+    g1[c] = gG0 - gGk;
+    g2[c] = eps * gdGk - gdG0;
+  }
+}
+
+void or_reaction_field(const or_ctx* c, const double* u, const double* pts, int64_t np, double* field) {
+  const int64_t nv = c->nv;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < np; ++k) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < c->nf; ++j) {
+      const int32_t* f = &c->F[3 * j];
+      for (int m = 0; m < 4; ++m) {
+        double g1[3], g2[3];
+        or_kernel_grads(&pts[3 * k], &c->gy[12 * j + 3 * m], &c->gn[12 * j + 3 * m], c->eps, c->kappa, g1, g2);
+        for (int n = 0; n < 3; ++n) {
+          const double w = c->gW[12 * j + 3 * m + n];
+          for (int q = 0; q < 3; ++q) s[q] += w * (g1[q] * u[nv + f[n]] + g2[q] * u[f[n]]);
+        }
+      }
+    }
+    for (int q = 0; q < 3; ++q) field[3 * k + q] = -s[q];
+  }
+}
+
 /* E_sol in kcal/mol: (1/2) sum_k q_k phi_reac(x_k), with phi in the G-units
  * of the formulation converted by 4 pi C, C = 332.0716 kcal A/(mol e^2). */
 double or_energy(const or_ctx* c, const double* u) {
