@@ -65,6 +65,8 @@ OPS_PER_PAIR = 30
 OPS_PER_PAIR_ROW1 = 18  # row 1 only (reaction potential, energy): d, r^2, d.m, 1/r^2, v, 1 + kappa r,
 #                        the exp2 argument, P - 1 and the 4 operations of row 1
 MUFU_PER_PAIR = 2  # rsqrt.approx + ex2.approx
+OPS_PER_PAIR_FIELD = 28  # reaction field: d, r^2, d.m, 1/r^2, v, 1 + kappa r, exponent, P - 1, P - 1/eps,
+#                          1/r^3, beta (4), its and (P - 1/eps)/r^3 factors (2), 3-vector accumulation (6)
 # MUFU (XU) lanes per SM per clock: an rsqrt.approx.f32 throughput microbenchmark (independent
 # chains, CUDA events) measured 15.9 lane-operations per SM per clock on GB300 at 2070 MHz.
 MUFU_LANES_PER_SM = 16
@@ -495,8 +497,8 @@ def lobi_object(hobi, arrays, e1, e2, ka, tol, stream, sms, fmax):
 
 
 def reaction_object(hobi, arrays, e1, e2, ka, tol, stream, sms, fmax, n_points=16384, radius=8.0):
-    """Off-surface output: the reaction potential at n_points interior points from a solved handle,
-    FP32-bulk and FP64 (row-1 far field, N_points x N_nodes pairs per call)."""
+    """Off-surface output: the reaction potential and the reaction field at n_points interior points
+    from a solved handle, FP32-bulk and FP64 (N_points x N_nodes pairs per call)."""
     import numpy as np
     import torch
 
@@ -523,10 +525,25 @@ def reaction_object(hobi, arrays, e1, e2, ka, tol, stream, sms, fmax, n_points=1
         rec = {"call_ms": ev[0].elapsed_time(ev[1]) / reps, "farfield_ms": launch_s * 1e3, "pairs_per_s": pairs / launch_s}
         if ops:
             rec["frac_fp32_lane_peak"] = alu_fraction(launch_s, pairs, ops, lanes, sms, fmax)[2]
+        # the reaction field at the same points (whole call: points, gather, field kernel, reduction)
+        s.reaction_field(pts)
+        ev[0].record(stream)
+        for _ in range(reps):
+            fld = s.reaction_field(pts)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        call_s = ev[0].elapsed_time(ev[1]) / reps / 1e3
+        field_pairs = float(n_points) * s.n_nodes
+        rec["field_call_ms"] = call_s * 1e3
+        rec["field_pairs_per_s"] = field_pairs / call_s
+        if ops:
+            rec["field_frac_fp32_lane_peak"] = alu_fraction(call_s, field_pairs, OPS_PER_PAIR_FIELD, lanes, sms, fmax)[2]
         out[prec] = rec
         if prec == "fp32":
-            phi32 = phi.clone()
+            phi32, fld32 = phi.clone(), fld.clone()
     out["fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(phi32 - phi) / torch.linalg.norm(phi))
+    out["field_fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(fld32 - fld) / torch.linalg.norm(fld))
+    out["field_ops_per_pair"] = f"{OPS_PER_PAIR_FIELD} FP32 FMA-pipe + 2 MUFU"
     s.close()
     return out
 

@@ -196,6 +196,19 @@ int hobi_get_solution(hobi_t h, double* u);
  * points [n_points][3], phi [n_points] (formulation units). */
 int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, double* phi);
 
+/* Reaction field -grad phi_reac at n_points points off the surface: the gradient, with respect to
+ * the point, of the reaction potential above (the same regular-rule sum, differentiated term by
+ * term), from the handle's solution. The paper motivates accurate potentials and fields near the
+ * interface (Sec. 1) but prints no field formula; with d = x - y, E = exp(-kappa r) and
+ * P = E (1 + kappa r) each node contributes -[(P - 1) sigma d + (eps P - 1) m
+ * - (kappa^2 eps E + 3 (eps P - 1)/r^2)(d . m) d]/r^3, the gradient of its (1 - E)/r sigma
+ * + (eps P - 1)(d . m)/r^3 term.
+ * points [n_points][3] (A), field [n_points][3] (formulation units per A), both in the memory
+ * space of the handle's mem_device option. A point must not coincide with a quadrature node.
+ * HOBI scheme only (HOBI_ERR_ARG for LOBI-PB); HOBI_ERR_STATE without a solution;
+ * n_points == 0 returns HOBI_OK. */
+int hobi_reaction_field(hobi_t h, const double* points, int64_t n_points, double* field);
+
 /* Same result as hobi_reaction_potential, but the call allocates no device memory. The paper
  * has no counterpart. It is meant for callers that must not allocate once they are running: a
  * host whose device memory is owned by another allocator (a framework's caching pool holding the

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhobi.so")
-SOURCES = ["hobi_capi.cu", "hobi_batch.cu", "k_setup.cu", "k_farfield.cu", "k_gmres.cu", "k_batch.cu", "k_fast.cu"]
+SOURCES = ["hobi_capi.cu", "hobi_batch.cu", "k_setup.cu", "k_farfield.cu", "k_gmres.cu", "k_batch.cu", "k_fast.cu",
+           "k_field.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

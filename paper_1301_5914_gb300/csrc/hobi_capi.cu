@@ -862,6 +862,26 @@ int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, do
   return h->check_farfield();
 }
 
+int hobi_reaction_field(hobi_t h, const double* points, int64_t n_points, double* field) {
+  NvtxRange nvtx_range("hobi_reaction_field");
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (n_points < 0 || (n_points > 0 && (!points || !field))) return fail(HOBI_ERR_ARG, "bad points/field arguments");
+  if (h->scheme != HOBI_SCHEME_HOBI) return fail(HOBI_ERR_ARG, "the reaction field supports the HOBI scheme only");
+  if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
+  if (n_points == 0) return HOBI_OK;
+  if (n_points > (int64_t(1) << 28)) return fail(HOBI_ERR_ARG, "too many points");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->ensure_point_buffers(n_points));
+  HOBI_TRY(h->copy_in(h->pts_in, points, 3 * n_points));
+  HOBI_CK(launch_points((int)n_points, h->pts_in, 3, h->center, h->xs, h->ptgt32, h->ptgt64, h->stream));
+  h->launches += 1;
+  HOBI_TRY(h->field_dev(n_points, h->ptgt32, h->ptgt64, h->fld_pts));
+  HOBI_TRY(h->copy_out(field, h->fld_pts, 3 * n_points));
+  HOBI_TRY(h->finish());
+  return h->check_farfield();
+}
+
 int hobi_energy(hobi_t h, double* e_sol) {
   NvtxRange nvtx_range("hobi_energy");
   if (!h || !e_sol) return fail(HOBI_ERR_ARG, "NULL argument");

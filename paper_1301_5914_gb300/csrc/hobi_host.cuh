@@ -157,7 +157,7 @@ struct hobi_ctx {
   int* flags = nullptr;
   float4 *tgt32 = nullptr, *ctgt32 = nullptr, *src32 = nullptr, *ptgt32 = nullptr;
   double *tgt64 = nullptr, *ctgt64 = nullptr, *src64 = nullptr, *ptgt64 = nullptr;
-  double *part = nullptr, *ppart = nullptr, *phi_pts = nullptr, *pts_in = nullptr;
+  double *part = nullptr, *ppart = nullptr, *phi_pts = nullptr, *pts_in = nullptr, *fld_pts = nullptr;
   size_t ppart_elems = 0, pts_cap = 0;
   FarFieldPlan plan[2];  // [0] FP64, [1] FP32 -- collocation-point targets, both rows
   // iterate vectors
@@ -487,11 +487,12 @@ struct hobi_ctx {
   int ensure_point_buffers(int64_t np) {
     if ((size_t)np <= pts_cap) return HOBI_OK;
     const size_t cap = std::max<size_t>({(size_t)64, (size_t)np, 2 * pts_cap});
-    if (ptgt32) { release(ptgt32); release(ptgt64); release(phi_pts); release(pts_in); }
+    if (ptgt32) { release(ptgt32); release(ptgt64); release(phi_pts); release(pts_in); release(fld_pts); }
     HOBI_TRY(alloc(&ptgt32, 2 * cap));
     HOBI_TRY(alloc(&ptgt64, 8 * cap));
     HOBI_TRY(alloc(&phi_pts, cap));
     HOBI_TRY(alloc(&pts_in, 3 * cap));
+    HOBI_TRY(alloc(&fld_pts, 3 * cap));
     pts_cap = cap;
     return HOBI_OK;
   }
@@ -501,6 +502,18 @@ struct hobi_ctx {
     if (ppart) release(ppart);
     HOBI_TRY(alloc(&ppart, elems));
     ppart_elems = elems;
+    return HOBI_OK;
+  }
+
+  // -grad phi_reac at np targets already in (t32, t64), [np][3], from the current solution x
+  int field_dev(int64_t np, const float4* t32, const double* t64, double* field) {
+    const bool fp32 = precision == HOBI_FP32_BULK;
+    FarFieldPlan p = plan_farfield(fp32, (int)np, (int)n_pad, false, num_sms, field_blocks_per_sm(fp32, kappa), 0);
+    HOBI_TRY(ensure_ppart((size_t)p.chunks * 3 * (size_t)np));
+    HOBI_TRY(gather(fp32, x, nullptr, 0));
+    HOBI_CK(launch_field(fp32, p, t32, t64, src32, src64, eps, kappa, ppart, ff_err, stream));
+    HOBI_CK(launch_reduce_field((int)np, p.chunks, ppart, field, stream));
+    launches += 3;
     return HOBI_OK;
   }
 

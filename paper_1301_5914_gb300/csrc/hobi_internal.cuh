@@ -156,6 +156,14 @@ cudaError_t launch_combine(int nv, int chunks, const double* part, const int* F,
 cudaError_t launch_reduce_points(int np, int chunks, const double* part, double* phi, cudaStream_t s);
 cudaError_t launch_energy_sum(int nc, const double* Q, const double* phi, double* e, cudaStream_t s);
 
+// Reaction field -grad phi_reac at p.n_targets points (k_field.cu): per chunk of source tiles the
+// three components to part[chunk][3][n]; the FP32 plan is shape 0's (32 threads x 8 targets,
+// 128-node tiles), the FP64 plan the FP64 far field's. field[3 i + c] = sum over chunks.
+int field_blocks_per_sm(bool fp32, double kappa);
+cudaError_t launch_field(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, const float4* src32,
+                         const double* src64, double eps, double kappa, double* part, int* err, cudaStream_t s);
+cudaError_t launch_reduce_field(int np, int chunks, const double* part, double* field, cudaStream_t s);
+
 // ---- GMRES (k_gmres.cu) ----
 struct GmresState {
   int k;          // column being built in the current cycle
