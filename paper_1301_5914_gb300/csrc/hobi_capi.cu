@@ -295,21 +295,8 @@ int setup_impl(hobi_ctx* h, const double* vertices, const int32_t* faces, const 
     HOBI_TRY(h->alloc(&h->src32, 4 * h->n_pad));
     HOBI_TRY(h->alloc(&h->src64, 8 * h->n_pad));
     HOBI_CK(launch_node_gen((int)nf, h->F, h->V, h->Nv, h->elem, h->ny, h->nnu, h->nW, h->flags, h->stream));
-    // The autotuner times far-field launches, so a handle that tunes builds the table first.
-    int cached_shape = 0;
-    const bool tunes = h->ff_shape < 0 && h->autotune && h->fast_degree == 0 &&
-                       !tune_lookup(tune_key(h->device, h->scheme, h->nv, h->n_pad), &cached_shape);
-    if (!light && !tunes && h->precision == HOBI_FP32_BULK) {
-      HOBI_CK(cudaEventRecord(h->ev_tables, h->stream));
-      HOBI_CK(cudaStreamWaitEvent(h->aux, h->ev_tables, 0));
-      HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem,
-                                        h->ny, h->nnu, h->nW, h->eps, h->kappa, h->corr, h->aux, h->num_sms));
-      HOBI_CK(cudaEventRecord(h->ev_corr, h->aux));
-      h->corr_pending = true;
-    } else {
-      HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem,
-                                        h->ny, h->nnu, h->nW, h->eps, h->kappa, h->corr, h->stream));
-    }
+    HOBI_CK(launch_correction_entries((int)(3 * nf), h->entry_vertex, h->F, h->V, h->Nv, h->inc_face, h->elem, h->ny,
+                                      h->nnu, h->nW, h->eps, h->kappa, h->corr, h->stream));
     HOBI_CK(launch_rhs((int)nv, (int)nc, h->V, h->Nv, h->Q, h->eps1, h->b, h->stream));
     HOBI_CK(launch_targets((int)nv, h->V, h->Nv, h->center, h->xs, h->tgt32, h->tgt64, h->stream));
     HOBI_CK(launch_points((int)nc, h->Q, 4, h->center, h->xs, h->ctgt32, h->ctgt64, h->stream));
@@ -509,9 +496,6 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
-    if (e == cudaSuccess && !light) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !light) e = cudaEventCreateWithFlags(&h->ev_tables, cudaEventDisableTiming);
-    if (e == cudaSuccess && !light) e = cudaEventCreateWithFlags(&h->ev_corr, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
       r = fail(HOBI_ERR_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(e));
@@ -908,7 +892,6 @@ int hobi_get_correction(hobi_t h, int64_t* n_entries, int32_t* vertex, int32_t* 
   if (!vertex && !face && !coeff) return HOBI_OK;
   DeviceGuard guard(h->device);
   HOBI_TRY(h->enter());
-  HOBI_TRY(h->wait_corr());
   const size_t ne = (size_t)(3 * h->nf);
   if (vertex) HOBI_CK(cudaMemcpyAsync(vertex, h->entry_vertex, sizeof(int) * ne, cudaMemcpyDeviceToHost, h->stream));
   if (face) HOBI_CK(cudaMemcpyAsync(face, h->inc_face, sizeof(int) * ne, cudaMemcpyDeviceToHost, h->stream));

@@ -114,13 +114,6 @@ struct hobi_ctx {
   cudaStream_t user_stream = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
-  // The singular correction table (FP64) is first needed by the combine step of the first matvec.
-  // A handle that will not autotune builds it on `aux`, one warp per SM, while the first FP32 far
-  // field occupies the rest of each SM (the two use different pipes); ev_corr marks its end, and
-  // the first reader waits for it on the handle's stream (wait_corr).
-  cudaStream_t aux = nullptr;
-  cudaEvent_t ev_tables = nullptr, ev_corr = nullptr;
-  bool corr_pending = false;
   int mem_device = 0, precision = HOBI_FP32_BULK, restart = 50, use_graph = 1, scheme = HOBI_SCHEME_HOBI;
   int autotune = 1, tuned = 0, ff_shape = -1;
   // nv: collocation points (mesh vertices for HOBI, face centroids for LOBI); nv_mesh: mesh vertices
@@ -369,22 +362,12 @@ struct hobi_ctx {
   }
 
   // Au = A u with u = base + (*kptr) * ld when kptr is given (device pointers)
-  // Orders the handle's stream after the correction table's build (once; never during a capture)
-  int wait_corr() {
-    if (!corr_pending) return HOBI_OK;
-    if (capturing) return fail(HOBI_ERR_CUDA, "internal: correction table pending during graph capture");
-    HOBI_CK(cudaStreamWaitEvent(stream, ev_corr, 0));
-    corr_pending = false;
-    return HOBI_OK;
-  }
-
   int matvec_dev(const double* u, const int* kptr, int64_t ld, double* Au) {
     const bool fp32 = precision == HOBI_FP32_BULK;
     const bool lobi = scheme == HOBI_SCHEME_LOBI;
     const bool fast = fast_active(fp32);
     HOBI_TRY(gather(fp32, u, kptr, ld, fast));
     HOBI_TRY(farfield(fp32, plan[fp32], tgt32, tgt64, part, lobi, fast));
-    HOBI_TRY(wait_corr());  // the far field above runs beside the table's build
     HOBI_CK(launch_combine((int)nv, fast ? fast_chunks : plan[fp32].chunks, part, F, lobi ? zero_ptr : inc_ptr,
                            inc_face, corr, eps, u, kptr, ld, Au, stream));
     if (!capturing) launches += fast ? 5 : 3;
@@ -433,8 +416,7 @@ struct hobi_ctx {
 
   int run_iteration() {
     const int pi = precision == HOBI_FP32_BULK;
-    // the first iteration after set-up runs eagerly while the correction table may still be building
-    if (!use_graph || (prof && graph_timing_unavailable) || corr_pending) return iteration();
+    if (!use_graph || (prof && graph_timing_unavailable)) return iteration();
     cudaGraphExec_t& gx = graph[pi][prof ? 1 : 0];
     if (!gx) {
       cudaGraph_t gr = nullptr;
@@ -532,7 +514,6 @@ struct hobi_ctx {
 
   ~hobi_ctx() {
     if (stream) cudaStreamSynchronize(stream);
-    if (aux) cudaStreamSynchronize(aux);
     for (auto& row : graph)
       for (auto& gexec : row)
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -550,9 +531,6 @@ struct hobi_ctx {
     if (ev_out) cudaEventDestroy(ev_out);
     if (ev_t0) cudaEventDestroy(ev_t0);
     if (ev_t1) cudaEventDestroy(ev_t1);
-    if (ev_tables) cudaEventDestroy(ev_tables);
-    if (ev_corr) cudaEventDestroy(ev_corr);
-    if (aux) cudaStreamDestroy(aux);
     if (stream) cudaStreamDestroy(stream);
   }
 };

@@ -71,7 +71,7 @@ cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double*
 cudaError_t launch_correction_entries(int n_entries, const int* vert, const int* F, const double* V,
                                       const double* Nv, const int* inc_face, const double* elem, const double* ny,
                                       const double* nnu, const double* nW, double eps, double kappa, double* corr,
-                                      cudaStream_t s, int warps = 0);  // warps > 0: that many one-warp blocks
+                                      cudaStream_t s);
 // LOBI-PB flat-face centroids, unit normals and areas
 cudaError_t launch_lobi_geometry(int nf, const int* F, const double* V, double* ny, double* nnu, double* nW,
                                  int* flags, cudaStream_t s);

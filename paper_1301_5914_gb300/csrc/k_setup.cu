@@ -364,7 +364,7 @@ __global__ void k_vertex_of_entry(int nv, const int* ptr, int* vert) {
   for (int e = ptr[i]; e < ptr[i + 1]; ++e) vert[e] = i;
 }
 
-// One thread per (vertex i, incident face j) entry; a grid smaller than the entry count strides.
+// One thread per (vertex i, incident face j) entry.
 __global__ void k_correction(int n_entries, const int* vert, const int* F, const double* V, const double* Nv,
                              const int* inc_face, const double* elem, const double* ny, const double* nnu,
                              const double* nW, KernelConsts kc, SingularRule rule, double* corr) {
@@ -541,7 +541,7 @@ cudaError_t launch_node_gen(int nf, const int* F, const double* V, const double*
 cudaError_t launch_correction_entries(int n_entries, const int* vert, const int* F, const double* V,
                                       const double* Nv, const int* inc_face, const double* elem, const double* ny,
                                       const double* nnu, const double* nW, double eps, double kappa, double* corr,
-                                      cudaStream_t s, int warps) {
+                                      cudaStream_t s) {
   // 4-point Gauss-Legendre on [0, 1]: nodes 1/2 (1 -+ sqrt(3/7 +- (2/7) sqrt(6/5))), weights
   // (18 -+ sqrt(30))/72 for the outer / inner pair
   const double t = 2.0 / 7.0 * std::sqrt(1.2);
@@ -562,11 +562,8 @@ cudaError_t launch_correction_entries(int n_entries, const int* vert, const int*
   kc.kappa = kappa;
   kc.c256 = -ff::kExpTable * 1.44269504088896340735992468100 * kappa;
   if (n_entries <= 0) return cudaSuccess;
-  if (warps > 0)
-    k_correction<<<warps, 32, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, kc, rule, corr);
-  else
-    k_correction<<<nblk(n_entries, 64), 64, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, kc, rule,
-                                                      corr);
+  k_correction<<<nblk(n_entries, 64), 64, 0, s>>>(n_entries, vert, F, V, Nv, inc_face, elem, ny, nnu, nW, kc, rule,
+                                                    corr);
   return cudaGetLastError();
 }
 
