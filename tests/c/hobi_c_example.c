@@ -94,12 +94,19 @@ int main(int argc, char** argv) {
     int r = hobi_solve(h, 1e-8, 200, phi, dphi, &info);
     double e = 0.0;
     if (r == HOBI_OK) r = hobi_energy(h, &e);
+    /* reaction potential and field at the centre and at an interior point */
+    const double pts[6] = {0.0, 0.0, 0.0, 0.3 * R, 0.2 * R, -0.1 * R};
+    double pr[2] = {0.0, 0.0}, fr[6] = {0.0};
+    if (r == HOBI_OK) r = hobi_reaction_potential(h, pts, 2, pr);
+    if (r == HOBI_OK) r = hobi_reaction_field(h, pts, 2, fr);
     if (r != HOBI_OK) {
-      fprintf(stderr, "solve/energy: %s\n", hobi_last_error());
+      fprintf(stderr, "solve/energy/potential/field: %s\n", hobi_last_error());
       status = 3;
     }
     printf("%s vertices %d faces %d iterations %d E_sol %.8f born %.8f\n", prec == 0 ? "fp64" : "fp32", m.nv, nf,
            info.iterations, e, born);
+    printf("%s phi_reac %.10e %.10e field %.6e %.6e %.6e %.6e %.6e %.6e\n", prec == 0 ? "fp64" : "fp32", pr[0], pr[1],
+           fr[0], fr[1], fr[2], fr[3], fr[4], fr[5]);
     free(phi);
     free(dphi);
     hobi_destroy(h);

@@ -43,3 +43,14 @@ def test_c_example_born_sphere(tmp_path):
     e64, e32, born = float(rows[0][4]), float(rows[1][4]), float(rows[0][5])
     assert abs(e64 - born) <= 2e-3 * abs(born)
     assert abs(e32 - e64) <= 1e-5 * abs(e64)
+    # the energy is (1/2) 4 pi C q phi_reac at the charge (the centre); inside a sphere with a centred
+    # charge the reaction potential is constant, so the field vanishes up to the discretisation error
+    pots = re.findall(r"(fp64|fp32) phi_reac (\S+) (\S+) field (.*)", r.stdout)
+    assert [x[0] for x in pots] == ["fp64", "fp32"]
+    for (prec, p0, p1, fld), e in zip(pots, (e64, e32)):
+        p0, p1 = float(p0), float(p1)
+        f = [float(v) for v in fld.split()]
+        # FP32: the energy's and the potential's far-field plans chunk the sources differently
+        assert abs(0.5 * 4 * 3.141592653589793 * 332.0716 * p0 - e) <= (1e-9 if prec == "fp64" else 1e-6) * abs(e)
+        assert abs(p1 - p0) <= 5e-3 * abs(p0)
+        assert max(abs(v) for v in f) * 2.0 <= 1e-2 * abs(p0), (prec, f, p0)
