@@ -292,7 +292,6 @@ __global__ void k_fast_targets(int nv, const int* __restrict__ tmap, const float
 
 constexpr int kUpThreads = 128;
 constexpr int kUpNodes = 64;  // nodes whose basis values are staged per pass
-constexpr int kMaxN1 = kFastMaxDegree + 1;
 
 // Partial proxy densities (sigma/eps, m) of one work item: nodes [n0, n_end) (tree order) of a
 // proxy cluster with Chebyshev axes ax and half-extents hf, to out[p], p = (i N1 + j) N1 + k.
