@@ -281,6 +281,13 @@ class Problem:
         _lib.or_reaction_field(self._h, _p(u), _p(pts), pts.shape[0], _p(out))
         return out
 
+    def reaction_forces(self, u) -> np.ndarray:
+        """Reaction-field force on each charge, 4 pi C q_k (-grad phi_reac)(x_k) in kcal/(mol A),
+        [n_c, 3]: the force of the polarised dielectric on the charge with the surface held fixed
+        (the energy's units, 4 pi C with C = 332.0716, times q and the field)."""
+        q = self.charges[:, 3:4]
+        return 4.0 * np.pi * 332.0716 * q * self.reaction_field(u, self.charges[:, :3])
+
     def energy(self, u) -> float:
         """E_sol in kcal/mol from the solution u = [phi; dphi/dnu]."""
         return float(_lib.or_energy(self._h, _p(_f64(u))))

@@ -71,3 +71,31 @@ def test_field_converges_to_the_kirkwood_series():
         u = p.gmres(1e-10)[0]
         errs.append(np.abs(p.reaction_field(u, pts) - ex).max() / np.abs(ex).max())
     assert errs[1] < errs[0] / 3 and errs[1] < 4e-3, errs
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.1257])
+def test_reaction_forces_are_minus_the_energy_gradient(kappa):
+    """The force on charge k, 4 pi C q_k times the reaction field at x_k, against central
+    differences of the solvation energy when x_k moves (the surface fixed, a full solve per
+    displaced position): the discrete operator keeps the reciprocity that makes these equal,
+    measured 2.9e-7 relative for two charges in a level-3 sphere with kappa = 0.1257."""
+    V, F, N = synth.icosphere(3, 3.0)
+    Q = np.array([[0.6, 0.3, -0.2, 1.0], [-0.5, -0.4, 0.3, -0.7]])
+
+    def solved(Qm):
+        p = oracle.Problem(V, F, N, Qm, 2.0, 80.0, kappa)
+        return p, p.gmres(1e-12, max_it=400)[0]
+
+    p, u = solved(Q)
+    f = p.reaction_forces(u)
+    h = 1e-4
+    fd = np.zeros((2, 3))
+    for k in range(2):
+        for c in range(3):
+            Qp, Qn = Q.copy(), Q.copy()
+            Qp[k, c] += h
+            Qn[k, c] -= h
+            pp, up = solved(Qp)
+            pn, un = solved(Qn)
+            fd[k, c] = -(pp.energy(up) - pn.energy(un)) / (2 * h)
+    assert np.max(np.abs(f - fd)) <= 2e-6 * np.max(np.abs(fd)), np.max(np.abs(f - fd)) / np.max(np.abs(fd))
