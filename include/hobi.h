@@ -209,6 +209,14 @@ int hobi_reaction_potential(hobi_t h, const double* points, int64_t n_points, do
  * n_points == 0 returns HOBI_OK. */
 int hobi_reaction_field(hobi_t h, const double* points, int64_t n_points, double* field);
 
+/* Reaction-field force on every charge, 4 pi C q_k (-grad phi_reac)(x_k) with C = 332.0716: the
+ * force of the polarised solvent on charge k with the dielectric surface held fixed, in
+ * kcal/(mol A) (the units of E_sol of Eq. (23) per A). The paper computes energies only; for a
+ * fixed surface this is minus the gradient of E_sol with respect to x_k.
+ * forces [n_c][3], in the memory space of the handle's mem_device option. HOBI scheme only;
+ * HOBI_ERR_STATE without a solution; a handle without charges returns HOBI_OK. */
+int hobi_reaction_forces(hobi_t h, double* forces);
+
 /* Same result as hobi_reaction_potential, but the call allocates no device memory. The paper
  * has no counterpart. It is meant for callers that must not allocate once they are running: a
  * host whose device memory is owned by another allocator (a framework's caching pool holding the

@@ -866,6 +866,24 @@ int hobi_reaction_field(hobi_t h, const double* points, int64_t n_points, double
   return h->check_farfield();
 }
 
+int hobi_reaction_forces(hobi_t h, double* forces) {
+  NvtxRange nvtx_range("hobi_reaction_forces");
+  if (!h) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (h->scheme != HOBI_SCHEME_HOBI) return fail(HOBI_ERR_ARG, "the reaction forces support the HOBI scheme only");
+  if (!h->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve or hobi_set_solution first");
+  if (h->nc == 0) return HOBI_OK;
+  if (!forces) return fail(HOBI_ERR_ARG, "forces is NULL");
+  DeviceGuard guard(h->device);
+  HOBI_TRY(h->enter());
+  HOBI_TRY(h->ensure_point_buffers(h->nc));
+  HOBI_TRY(h->field_dev(h->nc, h->ctgt32, h->ctgt64, h->fld_pts));
+  HOBI_CK(launch_charge_forces((int)h->nc, h->Q, h->fld_pts, h->fld_pts, h->stream));
+  h->launches += 1;
+  HOBI_TRY(h->copy_out(forces, h->fld_pts, 3 * h->nc));
+  HOBI_TRY(h->finish());
+  return h->check_farfield();
+}
+
 int hobi_energy(hobi_t h, double* e_sol) {
   NvtxRange nvtx_range("hobi_energy");
   if (!h || !e_sol) return fail(HOBI_ERR_ARG, "NULL argument");

@@ -163,6 +163,8 @@ int field_blocks_per_sm(bool fp32, double kappa);
 cudaError_t launch_field(bool fp32, const FarFieldPlan& p, const float4* t32, const double* t64, const float4* src32,
                          const double* src64, double eps, double kappa, double* part, int* err, cudaStream_t s);
 cudaError_t launch_reduce_field(int np, int chunks, const double* part, double* field, cudaStream_t s);
+// f[3 k + c] = 4 pi C q_k field[3 k + c], charges Q[n_c][4] (x, y, z, q)
+cudaError_t launch_charge_forces(int nc, const double* Q, const double* field, double* f, cudaStream_t s);
 
 // ---- GMRES (k_gmres.cu) ----
 struct GmresState {

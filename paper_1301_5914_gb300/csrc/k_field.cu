@@ -196,6 +196,15 @@ __global__ void k_reduce_field(int np, int chunks, const double* __restrict__ pa
   }
 }
 
+// Reaction-field force on each charge: f[3 k + c] = 4 pi C q_k field[3 k + c] (kcal/(mol A));
+// f may be field itself (each thread reads and writes only its own three entries)
+__global__ void k_charge_forces(int nc, const double* __restrict__ Q, const double* field, double* f) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nc) return;
+  const double s = 4.0 * kPi * kCoulomb * Q[4 * (size_t)k + 3];
+  for (int c = 0; c < 3; ++c) f[3 * (size_t)k + c] = s * field[3 * (size_t)k + c];
+}
+
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -238,6 +247,12 @@ cudaError_t launch_field(bool fp32, const FarFieldPlan& p, const float4* t32, co
       k_field64<false><<<grid, kFF64Threads, 0, s>>>(t64, p.n_targets, src64, p.n_tiles, p.tiles_per_chunk, cs,
                                                       scale, part);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_charge_forces(int nc, const double* Q, const double* field, double* f, cudaStream_t s) {
+  if (nc <= 0) return cudaSuccess;
+  k_charge_forces<<<nblk(nc, 256), 256, 0, s>>>(nc, Q, field, f);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
 EXPORTS = [
     "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
     "hobi_solve", "hobi_solve_from", "hobi_solve_refined", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
-    "hobi_reaction_potential_noalloc", "hobi_reaction_field", "hobi_energy",
+    "hobi_reaction_potential_noalloc", "hobi_reaction_field", "hobi_reaction_forces", "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
     "hobi_fast_info", "hobi_fast_plan_stats", "hobi_fp64_pair_functions", "hobi_check_tile_wait_timeout",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_get_solution.argtypes = [vp, dp]
     lib.hobi_reaction_potential.argtypes = [vp, dp, i64, dp]
     lib.hobi_reaction_field.argtypes = [vp, dp, i64, dp]
+    lib.hobi_reaction_forces.argtypes = [vp, dp]
     lib.hobi_reaction_potential_noalloc.argtypes = [vp, dp, i64, dp]
     lib.hobi_energy.argtypes = [vp, C.POINTER(C.c_double)]
     lib.hobi_get_nodes.argtypes = [vp, dp, dp, dp]
@@ -398,6 +399,12 @@ class Solver:
         out = self._out(3 * n)
         _check(self._lib.hobi_reaction_field(self._h, self._ptr(p), n, self._ptr(out)))
         return out.reshape(n, 3)
+
+    def reaction_forces(self):
+        """Reaction-field force on every charge, kcal/(mol A), [n_c, 3]."""
+        out = self._out(3 * self.nc)
+        _check(self._lib.hobi_reaction_forces(self._h, self._ptr(out)))
+        return out.reshape(self.nc, 3)
 
     def energy(self) -> float:
         e = C.c_double()

@@ -107,3 +107,26 @@ def test_field_arguments_and_state():
     with pytest.raises(hobi.HobiError) as ei:
         lo.reaction_field(np.zeros((4, 3)))
     assert ei.value.code == hobi.HOBI_ERR_ARG
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 5e-5)])
+def test_reaction_forces_match_oracle(case, prec, tol):
+    """4 pi C q_k times the reaction field at each charge (kcal/(mol A)) against the oracle's."""
+    V, F, N, Q, e1, e2, ka, orc, u, pts = case
+    ref = orc.reaction_forces(u)
+    s = hobi.Solver(V, F, N, Q, e1, e2, ka, precision=prec)
+    s.set_solution(u)
+    f = s.reaction_forces()
+    assert f.shape == (Q.shape[0], 3)
+    assert np.max(np.abs(f - ref)) <= tol * np.max(np.abs(ref)), np.max(np.abs(f - ref)) / np.max(np.abs(ref))
+    s.close()
+
+
+def test_reaction_forces_without_charges_or_solution():
+    V, F, N = synth.icosphere(2, 2.0)
+    s = hobi.Solver(V, F, N, np.zeros((0, 4)), 1.0, 80.0, 0.1, precision="fp64")
+    with pytest.raises(hobi.HobiError) as ei:
+        s.reaction_forces()
+    assert ei.value.code == hobi.HOBI_ERR_STATE
+    s.solve(1e-8, 50, raise_on_fail=False)
+    assert s.reaction_forces().shape == (0, 3)
