@@ -356,6 +356,10 @@ int hobi_solve_batch(hobi_batch_t b, double tol, int32_t max_it, double* phi, do
 /* Solvation energy of every molecule (Eq. (23)), e_sol[n_mol] HOST, kcal/mol. */
 int hobi_energy_batch(hobi_batch_t b, double* e_sol);
 
+/* Reaction-field force on every charge of every molecule, as hobi_reaction_forces:
+ * forces [sum n_c][3] HOST, kcal/(mol A), molecule blocks at charge_offsets. */
+int hobi_reaction_forces_batch(hobi_batch_t b, double* forces);
+
 /* Timing of the batched far-field launches, as hobi_profile_enable / hobi_profile_read
  * (pairs counts only the molecules still iterating at each launch; for a molecule on fast
  * summation, its node and proxy pair evaluations; the timed span includes the treecode's

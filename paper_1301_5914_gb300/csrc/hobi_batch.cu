@@ -670,6 +670,44 @@ int hobi_energy_batch(hobi_batch_t B, double* e_sol) {
   return HOBI_OK;
 }
 
+int hobi_reaction_forces_batch(hobi_batch_t B, double* forces) {
+  NvtxRange nvtx_range("hobi_reaction_forces_batch");
+  if (!B) return fail(HOBI_ERR_ARG, "NULL handle");
+  if (!B->have_solution) return fail(HOBI_ERR_STATE, "no solution: call hobi_solve_batch first");
+  int64_t total = 0;
+  for (hobi_t h : B->subs) total += h->nc;
+  if (total == 0) return HOBI_OK;
+  if (!forces) return fail(HOBI_ERR_ARG, "forces is NULL");
+  DeviceGuard guard(B->device);
+  for (int i = 0; i < B->nmol; ++i) {
+    hobi_t h = B->subs[i];
+    h->precision = B->precision;
+    HOBI_CK(cudaMemcpyAsync(h->x, B->x + B->mols_h[i].u_off, sizeof(double) * 2 * h->nv, cudaMemcpyDeviceToDevice,
+                            B->stream));
+  }
+  HOBI_CK(cudaStreamSynchronize(B->stream));
+  // every member's field and forces on its own stream, then the copies in molecule order
+  for (hobi_t h : B->subs) {
+    h->have_solution = true;
+    if (h->nc == 0) continue;
+    HOBI_TRY(h->enter());
+    HOBI_TRY(h->ensure_point_buffers(h->nc));
+    HOBI_TRY(h->field_dev(h->nc, h->ctgt32, h->ctgt64, h->fld_pts));
+    HOBI_CK(launch_charge_forces((int)h->nc, h->Q, h->fld_pts, h->fld_pts, h->stream));
+    h->launches += 1;
+    HOBI_TRY(h->leave());
+  }
+  int64_t off = 0;
+  for (hobi_t h : B->subs) {
+    if (h->nc == 0) continue;
+    HOBI_CK(cudaStreamSynchronize(h->stream));
+    HOBI_TRY(h->check_farfield());
+    HOBI_CK(cudaMemcpy(forces + 3 * off, h->fld_pts, sizeof(double) * 3 * h->nc, cudaMemcpyDeviceToHost));
+    off += h->nc;
+  }
+  return HOBI_OK;
+}
+
 int hobi_batch_profile_enable(hobi_batch_t B, int32_t on) {
   if (!B) return fail(HOBI_ERR_ARG, "NULL handle");
   B->prof = on != 0;

@@ -35,7 +35,8 @@ KCAL_PER_MOL_E = 4.0 * np.pi * 332.0716
 EXPORTS = [
     "hobi_default_options", "hobi_setup", "hobi_set_precision", "hobi_sizes", "hobi_matvec", "hobi_rhs",
     "hobi_solve", "hobi_solve_from", "hobi_solve_refined", "hobi_set_solution", "hobi_get_solution", "hobi_reaction_potential",
-    "hobi_reaction_potential_noalloc", "hobi_reaction_field", "hobi_reaction_forces", "hobi_energy",
+    "hobi_reaction_potential_noalloc", "hobi_reaction_field", "hobi_reaction_forces", "hobi_reaction_forces_batch",
+    "hobi_energy",
     "hobi_get_nodes", "hobi_get_correction", "hobi_profile_enable", "hobi_profile_read", "hobi_kernel_launches", "hobi_plan_info",
     "hobi_fast_info", "hobi_fast_plan_stats", "hobi_fp64_pair_functions", "hobi_check_tile_wait_timeout",
     "hobi_destroy", "hobi_last_error", "hobi_setup_batch", "hobi_batch_sizes", "hobi_batch_set_precision",
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.hobi_reaction_potential.argtypes = [vp, dp, i64, dp]
     lib.hobi_reaction_field.argtypes = [vp, dp, i64, dp]
     lib.hobi_reaction_forces.argtypes = [vp, dp]
+    lib.hobi_reaction_forces_batch.argtypes = [vp, dp]
     lib.hobi_reaction_potential_noalloc.argtypes = [vp, dp, i64, dp]
     lib.hobi_energy.argtypes = [vp, C.POINTER(C.c_double)]
     lib.hobi_get_nodes.argtypes = [vp, dp, dp, dp]
@@ -591,6 +593,12 @@ class BatchSolver:
         e = np.zeros(self.n_mol, dtype=np.float64)
         _check(self._lib.hobi_energy_batch(self._h, e.ctypes.data))
         return e
+
+    def reaction_forces(self):
+        """Reaction-field forces on the charges, one [n_c, 3] array per molecule (kcal/(mol A))."""
+        f = np.zeros((int(self.charge_off[-1]), 3), dtype=np.float64)
+        _check(self._lib.hobi_reaction_forces_batch(self._h, f.ctypes.data))
+        return [f[self.charge_off[m]:self.charge_off[m + 1]] for m in range(self.n_mol)]
 
     def kernel_launches(self) -> int:
         n = C.c_int64()

@@ -148,3 +148,21 @@ def test_batch_reports_first_bad_member_in_index_order():
         with pytest.raises(hobi.HobiError) as ei:
             hobi.BatchSolver(mols, 1.0, 80.0, 0.0)
         assert ei.value.code == hobi.HOBI_ERR_MESH and "molecule 3:" in str(ei.value)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_batch_reaction_forces_equal_single_handles(molecules, prec, tol):
+    """hobi_reaction_forces_batch: per molecule the forces a single handle computes from the same
+    solution (the members queue their field kernels on their own streams)."""
+    bs = hobi.BatchSolver(molecules, EPS1, EPS2, KAPPA, precision=prec)
+    phis, dphis, info = bs.solve(1e-8, 200)
+    forces = bs.reaction_forces()
+    assert len(forces) == len(molecules)
+    for i, (V, F, N, Q) in enumerate(molecules):
+        s = hobi.Solver(V, F, N, Q, EPS1, EPS2, KAPPA, precision=prec)
+        s.set_solution(np.concatenate([phis[i], dphis[i]]))
+        ref = s.reaction_forces()
+        assert forces[i].shape == ref.shape == (Q.shape[0], 3)
+        assert np.max(np.abs(forces[i] - ref)) <= tol * np.max(np.abs(ref))
+        s.close()
+    bs.close()
