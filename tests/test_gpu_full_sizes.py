@@ -1,5 +1,6 @@
 """Parity at the full sizes of the two largest workloads, in the launch configurations bench.py
-times: the C5 two-globule complex (59,888 vertices x 479,088 nodes; 1,061 sampled rows) and the
+times: the C5 two-globule complex (59,888 vertices x 479,088 nodes; 1,061 sampled rows, plus the
+reaction field at 96 points and the forces on 64 of its charges) and the
 C4 batch of 64 molecules (at least 32 rows of every molecule), on rows the oracle evaluates one
 by one: the edges of every 256-target block (first and last row, both sides of the first thread
 stride) plus seeded random rows; and the empty-charge edge case.
@@ -59,6 +60,17 @@ def test_c5_complex_sampled_rows():
     s.set_solution(u)
     e_ref = orc.energy(u)
     assert abs(s.energy() - e_ref) <= 1e-5 * abs(e_ref)
+    # reaction field at 96 points (inside and outside the surface) and the forces on 64 of the
+    # 6,000 charges, at full size, against the oracle
+    rng = np.random.default_rng(9)
+    c = V.mean(axis=0)
+    pts = np.concatenate([Q[rng.choice(Q.shape[0], 64, replace=False), :3] + 0.3 * rng.normal(size=(64, 3)),
+                          c + rng.normal(size=(32, 3)) * 40.0])
+    f_ref = orc.reaction_field(u, pts)
+    assert np.max(np.abs(s.reaction_field(pts) - f_ref)) <= 5e-5 * np.max(np.abs(f_ref))
+    k = np.sort(rng.choice(Q.shape[0], 64, replace=False))
+    fk_ref = 4 * np.pi * 332.0716 * Q[k, 3:4] * orc.reaction_field(u, Q[k, :3])
+    assert np.max(np.abs(s.reaction_forces()[k] - fk_ref)) <= 5e-5 * np.max(np.abs(fk_ref))
     # fast summation at full size: on this smooth u the far (approximated) part carries more of
     # each row than on a random vector, so the treecode's deviation from the direct operator is
     # larger here (measured 1.2e-5 relative L2, against 7.8e-7 on a random u); energy within 1e-5
