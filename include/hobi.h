@@ -32,7 +32,10 @@
  *    stream). Calls return after their results are complete on that stream
  *    as far as host pointers are concerned; device-pointer outputs are
  *    complete in stream order.
- *  - A handle is not thread-safe: one thread at a time per handle.
+ *  - A handle is not thread-safe: one thread at a time per handle. Different
+ *    handles may be set up, used and destroyed from different threads at the
+ *    same time (the library's shared state -- memory pool, pinned slots,
+ *    autotuner cache -- is locked; a batch builds its molecules that way).
  */
 #ifndef HOBI_H_
 #define HOBI_H_
