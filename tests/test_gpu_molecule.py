@@ -73,6 +73,15 @@ def test_molecule_matvec_sampled_rows(molecule):
     _check_rows(s.matvec(u), orc, u, rows, 1e-4)
 
 
+def test_molecule_rhs_matches_oracle(molecule):
+    """Eq. (11) at 19,944 vertices with 1,000 charges (two-float Coulomb sums) against the oracle."""
+    V, F, N, Q, e1, e2, ka = molecule
+    ref = oracle.Problem(V, F, N, Q, e1, e2, ka).rhs()
+    b = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp64").rhs()
+    assert np.linalg.norm(b - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.max(np.abs(b - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
 def test_molecule_solve_fp32_vs_fp64_and_energy(molecule):
     V, F, N, Q, e1, e2, ka = molecule
     s = hobi.Solver(V, F, N, Q, e1, e2, ka, precision="fp64")
