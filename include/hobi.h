@@ -7,8 +7,9 @@
  * Triangulation", Sec. 2.1, Eqs. (8)/(9)) on a closed triangulated
  * molecular surface, with curved elements built from vertex normals
  * (Sec. 2.2), 4-point quadrature on regular triangles, 16-point regularised
- * Gauss-Legendre quadrature on singular triangles (Sec. 2.3), GMRES, and the
- * electrostatic solvation energy (Sec. 2.5, Eq. (23)).
+ * Gauss-Legendre quadrature on singular triangles (Sec. 2.3), GMRES, the
+ * electrostatic solvation energy (Sec. 2.5, Eq. (23)), and the reaction
+ * potential, reaction field and reaction-field forces it implies.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -25,7 +26,7 @@
  *    Eq. (10); only eps2/eps1 makes Eqs. (8)/(9) consistent with the jump
  *    condition). Source terms carry 1/eps1.
  *  - Array arguments (vertices, faces, normals, charges, u, Au, phi, dphi,
- *    points, potentials) are HOST pointers when opt.mem_device == 0 and
+ *    points, potentials, fields, forces) are HOST pointers when opt.mem_device == 0 and
  *    DEVICE pointers (on the handle's device) when opt.mem_device == 1.
  *    Scalar outputs (energy, info, counts) are always host pointers.
  *  - Work is ordered on opt.stream (a cudaStream_t; NULL = the legacy default
