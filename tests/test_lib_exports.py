@@ -47,3 +47,6 @@ def test_null_arguments_rejected_without_gpu():
     assert b"non-NULL" in hobi._lib.hobi_last_error()
     assert hobi._lib.hobi_matvec(None, None, None) == hobi.HOBI_ERR_ARG
     assert hobi._lib.hobi_energy(None, None) == hobi.HOBI_ERR_ARG
+    assert hobi._lib.hobi_reaction_field(None, None, 0, None) == hobi.HOBI_ERR_ARG
+    assert hobi._lib.hobi_reaction_forces(None, None) == hobi.HOBI_ERR_ARG
+    assert hobi._lib.hobi_reaction_forces_batch(None, None) == hobi.HOBI_ERR_ARG
