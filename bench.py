@@ -3,9 +3,9 @@
 
 One step = the whole hot path on one synthetic molecule with its inputs resident
 in HBM: hobi_setup (mesh validation, adjacency, curved-element nodes, singular
-correction table, right-hand side), hobi_solve (GMRES to 1e-6: per iteration
-gather + far-field pair sum + correction/diagonal + FP64 Arnoldi/Givens) and
-hobi_energy. Workload: Kirkwood sphere of radius 10 A, icosphere level 6
+correction table, right-hand side), hobi_solve (GMRES to 1e-6 on the diagonally
+scaled unknowns: per iteration the scaled Arnoldi vector, gather + far-field pair
+sum + correction/diagonal + FP64 Arnoldi/Givens) and hobi_energy. Workload: Kirkwood sphere of radius 10 A, icosphere level 6
 (81,920 curved triangles, 40,962 vertices, 327,680 quadrature nodes), 10 seeded
 charges uniform in a radius-8 ball, eps1 = 1, eps2 = 80, kappa = 0.1257 1/A;
 FP32-bulk far field.
