@@ -130,3 +130,18 @@ def test_reaction_forces_without_charges_or_solution():
     assert ei.value.code == hobi.HOBI_ERR_STATE
     s.solve(1e-8, 50, raise_on_fail=False)
     assert s.reaction_forces().shape == (0, 3)
+
+
+def test_field_of_a_fast_summation_handle_is_the_direct_sum():
+    """The reaction field always sums every node directly: a handle whose matvec uses the treecode
+    gives the same field as a direct handle from the same solution."""
+    V, F, N = synth.icosphere(5, 10.0)
+    Q = synth.ball_charges(10, 8.0, 2)
+    u = np.random.default_rng(4).normal(size=2 * V.shape[0])
+    pts = synth.ball_charges(300, 7.0, 5)[:, :3]
+    d = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32")
+    f = hobi.Solver(V, F, N, Q, 1.0, 80.0, 0.1257, precision="fp32", fast_degree=5, fast_theta=0.7)
+    d.set_solution(u)
+    f.set_solution(u)
+    assert np.array_equal(d.reaction_field(pts), f.reaction_field(pts))
+    assert np.array_equal(d.reaction_forces(), f.reaction_forces())
