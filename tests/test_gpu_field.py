@@ -86,6 +86,8 @@ def test_field_device_pointers_equal_host(case):
         b = sd.reaction_field(t(pts))
         assert isinstance(b, torch.Tensor) and b.shape == (pts.shape[0], 3)
         assert np.array_equal(a, b.cpu().numpy())
+        fd = sd.reaction_forces()
+        assert isinstance(fd, torch.Tensor) and np.array_equal(sh.reaction_forces(), fd.cpu().numpy())
 
 
 def test_field_arguments_and_state():
