@@ -273,7 +273,13 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   };
   const int nthreads = std::min(nmol, kSetupThreads);
   std::vector<std::thread> workers;
-  for (int t = 1; t < nthreads; ++t) workers.emplace_back(build);
+  for (int t = 1; t < nthreads; ++t) {
+    try {
+      workers.emplace_back(build);
+    } catch (...) {  // no thread to be had: the threads that exist take the remaining molecules
+      break;
+    }
+  }
   build();
   for (auto& t : workers) t.join();
   B->subs = made;
