@@ -265,10 +265,14 @@ int batch_setup_impl(hobi_batch_ctx* B, const double* vertices, const int64_t* v
   auto build = [&]() {
     for (int m = next.fetch_add(1); m < nmol; m = next.fetch_add(1)) {
       const int64_t nv = v_off[m + 1] - v_off[m], nf = f_off[m + 1] - f_off[m], nc = c_off[m + 1] - c_off[m];
-      rc[m] = create_handle(vertices + 3 * v_off[m], nv, faces + 3 * f_off[m], nf, normals + 3 * v_off[m],
-                            nc > 0 ? charges + 4 * c_off[m] : nullptr, nc, eps1, eps2, B->kappa, &so, true,
-                            &made[m], &B->arena);
-      if (rc[m] != HOBI_OK) msg[m] = g_err;
+      rc[m] = host_guard([&] {
+        const int r = create_handle(vertices + 3 * v_off[m], nv, faces + 3 * f_off[m], nf, normals + 3 * v_off[m],
+                                    nc > 0 ? charges + 4 * c_off[m] : nullptr, nc, eps1, eps2, B->kappa, &so, true,
+                                    &made[m], &B->arena);
+        if (r != HOBI_OK) msg[m] = g_err;
+        return r;
+      });
+      if (rc[m] != HOBI_OK && msg[m].empty()) msg[m] = g_err;
     }
   };
   const int nthreads = std::min(nmol, kSetupThreads);
@@ -487,7 +491,8 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
   }
   o.device = dev;
   DeviceGuard guard(dev);
-  hobi_batch_ctx* B = new hobi_batch_ctx();
+  hobi_batch_ctx* B = new (std::nothrow) hobi_batch_ctx();
+  if (!B) return fail(HOBI_ERR_NOMEM, "host allocation of the batch handle failed");
   B->device = dev;
   B->arena.device = dev;
   B->arena.chunk = size_t(32) << 20;  // one arena for all members: larger blocks
@@ -519,8 +524,10 @@ int hobi_setup_batch(int32_t n_mol, const double* vertices, const int64_t* verte
     B->arena.home = B->stream;
     r = B->enter();
     if (r != HOBI_OK) break;
-    r = batch_setup_impl(B, vertices, vertex_offsets, faces, face_offsets, vertex_normals, charges, charge_offsets, eps1,
-                         eps2, o);
+    r = host_guard([&] {
+      return batch_setup_impl(B, vertices, vertex_offsets, faces, face_offsets, vertex_normals, charges,
+                              charge_offsets, eps1, eps2, o);
+    });
     if (r != HOBI_OK) break;
     r = B->leave();
   } while (0);

@@ -503,7 +503,7 @@ int create_handle(const double* vertices, int64_t n_v, const int32_t* faces, int
     }
     r = h->enter();
     if (r != HOBI_OK) break;
-    r = setup_impl(h, vertices, faces, vertex_normals, charges, light);
+    r = host_guard([&] { return setup_impl(h, vertices, faces, vertex_normals, charges, light); });
     if (r != HOBI_OK) break;
     r = h->leave();
   } while (0);
@@ -550,7 +550,9 @@ int hobi_setup(const double* vertices, int64_t n_v, const int32_t* faces, int64_
                const double* charges, int64_t n_c, double eps1, double eps2, double kappa, const hobi_options* opt,
                hobi_t* out) {
   NvtxRange nvtx_range("hobi_setup");
-  return create_handle(vertices, n_v, faces, n_f, vertex_normals, charges, n_c, eps1, eps2, kappa, opt, false, out);
+  return host_guard([&] {
+    return create_handle(vertices, n_v, faces, n_f, vertex_normals, charges, n_c, eps1, eps2, kappa, opt, false, out);
+  });
 }
 
 int hobi_set_precision(hobi_t h, int32_t precision) {
@@ -792,19 +794,19 @@ extern "C" {
 
 int hobi_solve(hobi_t h, double tol, int32_t max_it, double* phi, double* dphi, hobi_solve_info* info) {
   NvtxRange nvtx_range("hobi_solve");
-  return solve_impl(h, nullptr, false, tol, max_it, phi, dphi, info);
+  return host_guard([&] { return solve_impl(h, nullptr, false, tol, max_it, phi, dphi, info); });
 }
 
 int hobi_solve_refined(hobi_t h, double tol, int32_t max_refine, int32_t max_it, double* phi, double* dphi,
                        hobi_solve_info* info) {
   NvtxRange nvtx_range("hobi_solve_refined");
-  return solve_refined_impl(h, tol, max_refine, max_it, phi, dphi, info);
+  return host_guard([&] { return solve_refined_impl(h, tol, max_refine, max_it, phi, dphi, info); });
 }
 
 int hobi_solve_from(hobi_t h, const double* u0, double tol, int32_t max_it, double* phi, double* dphi,
                     hobi_solve_info* info) {
   NvtxRange nvtx_range("hobi_solve_from");
-  return solve_impl(h, u0, true, tol, max_it, phi, dphi, info);
+  return host_guard([&] { return solve_impl(h, u0, true, tol, max_it, phi, dphi, info); });
 }
 
 int hobi_set_solution(hobi_t h, const double* u) {
@@ -964,14 +966,16 @@ int hobi_fast_plan_stats(const double* nodes, int64_t n_nodes, const double* tar
   if (n_nodes > INT32_MAX / 2 || n_targets > INT32_MAX / 2) return fail(HOBI_ERR_ARG, "too many points");
   if (degree < 2 || degree > kFastMaxDegree) return fail(HOBI_ERR_ARG, "degree must be 2..10");
   if (!(theta > 0.0 && theta <= 1.0)) return fail(HOBI_ERR_ARG, "theta must be in (0, 1]");
-  FastPlanHost P;
-  const double origin[3] = {0.0, 0.0, 0.0};
-  build_fast_plan(nodes, (int)n_nodes, targets, (int)n_targets, origin, 1.0, degree, theta, 1, 0, &P);
-  if (direct_pairs) *direct_pairs = P.direct_pairs;
-  if (approx_pairs) *approx_pairs = P.approx_pairs;
-  if (batches) *batches = (int32_t)P.batch.size();
-  if (proxy_clusters) *proxy_clusters = (int32_t)P.pc_offset.size();
-  return HOBI_OK;
+  return host_guard([&] {
+    FastPlanHost P;
+    const double origin[3] = {0.0, 0.0, 0.0};
+    build_fast_plan(nodes, (int)n_nodes, targets, (int)n_targets, origin, 1.0, degree, theta, 1, 0, &P);
+    if (direct_pairs) *direct_pairs = P.direct_pairs;
+    if (approx_pairs) *approx_pairs = P.approx_pairs;
+    if (batches) *batches = (int32_t)P.batch.size();
+    if (proxy_clusters) *proxy_clusters = (int32_t)P.pc_offset.size();
+    return (int)HOBI_OK;
+  });
 }
 
 int hobi_fp64_pair_functions(const double* x, int64_t n, double* rsqrt_x, double* exp_neg_x) {

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <climits>
 #include <mutex>
+#include <new>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string>
@@ -34,8 +35,24 @@ struct NvtxRange {
 extern thread_local std::string g_err;
 
 inline int fail(int code, const std::string& msg) {
-  g_err = msg;
+  try {
+    g_err = msg;
+  } catch (...) {  // out of host memory: keep the status, lose the message
+  }
   return code;
+}
+
+// Runs a body that allocates host memory and turns a C++ exception (a failed host allocation,
+// most likely) into a status, so that nothing throws across the C ABI.
+template <class F>
+int host_guard(F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(HOBI_ERR_NOMEM, "host memory allocation failed");
+  } catch (...) {
+    return fail(HOBI_ERR_CUDA, "unexpected host-side exception");
+  }
 }
 
 struct DeviceGuard {
